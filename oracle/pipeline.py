@@ -1,7 +1,7 @@
 """The online solve composed from the oracle's pieces, in the paper's order (Sec. II-B, III-A):
 priors from the seeds (Sec. IV-A) -> number of eigenvectors m from the seeds (Eq. alpha_1),
-unless fixed -> fast RW with the first m columns (Eqs. Fs, U_lin_comb) -> k refinement steps on
-Eq. (rw_eq) -> hard labels by the largest probability (ties to the lowest label, Sec. IV-A's
+unless fixed -> fast RW with the first m columns (Eqs. Fs, U_lin_comb) -> k damped-Jacobi
+refinement steps on Eq. (rw_eq) -> hard labels by the largest probability (ties to the lowest label, Sec. IV-A's
 conversion of a probabilistic segmentation).  Test infrastructure only.
 """
 from __future__ import annotations
@@ -19,7 +19,8 @@ def hard_labels(U):
 
 
 def online_solve(g, Q, lam, seed_idx, seed_lab, n_labels, gamma=1e-3, m=0, m_step=10, eps=0.1,
-                 refine_steps=3, normalized=True, P=None):
+                 refine_steps=3, normalized=True, P=None,
+                 refine_method="jacobi", omega=0.8):
     """Returns dict(U, labels, m, f, capped, P)."""
     if P is None:
         P = gaussian_priors(g.J, seed_idx, seed_lab, n_labels)
@@ -30,5 +31,6 @@ def online_solve(g, Q, lam, seed_idx, seed_lab, n_labels, gamma=1e-3, m=0, m_ste
         info.update(f=f, capped=capped)
     U = fast_rw(g, Q[:, :m], lam[:m], seed_idx, seed_lab, n_labels, P, gamma, normalized)
     if refine_steps > 0:
-        U, _ = refine(g, U, seed_idx, seed_lab, n_labels, P, gamma, refine_steps, normalized)
+        U, _ = refine(g, U, seed_idx, seed_lab, n_labels, P, gamma, refine_steps, normalized,
+                      refine_method, omega)
     return dict(U=U, labels=hard_labels(U), m=m, P=P, **info)

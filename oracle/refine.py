@@ -1,6 +1,15 @@
-"""Refinement of an approximate solution of Eq. (rw_eq) by k steps of Jacobi-preconditioned
-conjugate gradients (oracle, FP64).  The paper has no refinement step; it recovers accuracy
-lost to low-precision storage of the basis.  Test infrastructure only.
+"""Refinement of an approximate solution of Eq. (rw_eq) (oracle, FP64).  The paper has no
+refinement step; it recovers accuracy lost to low-precision storage of the basis.
+Test infrastructure only.
+
+Two refiners are restated:
+* ``jacobi``: k damped-Jacobi steps on the residual, x <- x + omega diag(A)^{-1} (b - A x).
+  Linear in the starting point, and its iteration matrix has max-norm
+  |1 - omega| + omega / (1 + gamma) <= 1 for 0 < omega <= 1 (rows of diag(A)^{-1} A), so a
+  perturbation of the start never grows in max-norm.  This is the default.
+* ``pcg``: k steps of Jacobi-preconditioned conjugate gradients (each column its own
+  recurrence).  Its step lengths depend on the start, so a small perturbation of the start can
+  grow; it is used to refine to a tolerance against the exact solve.
 
 The system is the one the fast RW approximates: with the normalized Laplacian (Sec. II-C)
     (L-hat_n + gamma I) U-hat_n = gamma P-hat_n - B-hat^T U-hat_s,   U = D^{-1/2} U-hat,
@@ -58,12 +67,31 @@ def pcg_steps(A, b, x0, steps):
     return x, hist
 
 
-def refine(g, U0, seed_idx, seed_lab, n_labels, P, gamma, steps, normalized=True):
-    """Start from U0 (N x l, e.g. the fast RW), run ``steps`` Jacobi-PCG steps on the hat
+def jacobi_steps(A, b, x0, steps, omega=0.8):
+    """k damped-Jacobi steps; returns x_k and the residual norms per step."""
+    x = np.array(x0, dtype=np.float64, copy=True)
+    Dinv = 1.0 / A.diagonal()
+    hist = []
+    for _ in range(steps):
+        r = b - A @ x
+        hist.append(np.linalg.norm(r, axis=0))
+        x += omega * Dinv[:, None] * r
+    hist.append(np.linalg.norm(b - A @ x, axis=0))
+    return x, hist
+
+
+def refine(g, U0, seed_idx, seed_lab, n_labels, P, gamma, steps, normalized=True,
+           method="jacobi", omega=0.8):
+    """Start from U0 (N x l, e.g. the fast RW), run ``steps`` refinement steps on the hat
     system, return (U, residual-norm history)."""
     A, b, n, sc = hat_system(g, seed_idx, seed_lab, n_labels, P, gamma, normalized)
     x0 = sc[n, None] * U0[n]
-    x, hist = pcg_steps(A, b, x0, steps)
+    if method == "jacobi":
+        x, hist = jacobi_steps(A, b, x0, steps, omega)
+    elif method == "pcg":
+        x, hist = pcg_steps(A, b, x0, steps)
+    else:
+        raise ValueError(method)
     U = np.array(U0, dtype=np.float64, copy=True)
     U[seed_idx] = onehot(seed_lab, n_labels)
     U[n] = x / sc[n, None]

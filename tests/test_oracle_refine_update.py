@@ -25,15 +25,38 @@ def test_cg_error_monotone_and_converges():
     xe = sc[n, None] * Ue[n]
     errs = []
     for k in range(0, 6):
-        U, _ = refine.refine(g, U0, si, sl, nl, P, gamma, k)
+        U, _ = refine.refine(g, U0, si, sl, nl, P, gamma, k, method="pcg")
         e = sc[n, None] * U[n] - xe
         errs.append(np.einsum("ij,ij->j", e, A @ e))     # A-norm error per column
     errs = np.array(errs)
     assert np.all(np.diff(errs, axis=0) <= 1e-14)        # CG: A-norm error never increases
-    U, _ = refine.refine(g, U0, si, sl, nl, P, gamma, 400)
+    U, _ = refine.refine(g, U0, si, sl, nl, P, gamma, 400, method="pcg")
     np.testing.assert_allclose(U, Ue, atol=1e-9)
-    U, _ = refine.refine(g, U0, si, sl, nl, P, gamma, 0)
+    U, _ = refine.refine(g, U0, si, sl, nl, P, gamma, 0, method="pcg")
     np.testing.assert_array_equal(U, U0)
+
+
+def test_jacobi_fixed_point_contraction_and_convergence():
+    """The exact solution is a fixed point; the max-norm distance between two runs from
+    different starts never grows (iteration-matrix max-norm <= 1); many steps converge."""
+    g, si, sl, nl, P = _case(seed=5)
+    gamma = 0.05
+    Ue = exact.exact_rw(g, si, sl, nl, P, gamma)
+    U, _ = refine.refine(g, Ue, si, sl, nl, P, gamma, 3)
+    np.testing.assert_allclose(U, Ue, atol=1e-13)
+    rng = np.random.default_rng(1)
+    n = exact.split(g.N, si)
+    A0 = Ue.copy(); A0[n] += 0.1 * rng.standard_normal((n.size, nl))
+    B0 = A0.copy(); B0[n] += 1e-3 * rng.standard_normal((n.size, nl))
+    prev = np.abs(A0 - B0).max()
+    for k in range(1, 6):
+        a, _ = refine.refine(g, A0, si, sl, nl, P, gamma, k)
+        b, _ = refine.refine(g, B0, si, sl, nl, P, gamma, k)
+        cur = np.abs(a - b).max()
+        assert cur <= prev * (1 + 1e-12)
+        prev = cur
+    U, _ = refine.refine(g, A0, si, sl, nl, P, gamma, 3000)
+    np.testing.assert_allclose(U, Ue, atol=1e-8)
 
 
 def test_values_unchanged_when_beta_unchanged():
