@@ -1,0 +1,294 @@
+/*
+ * rw.h — C ABI of a GB300 (sm_103a) implementation of the precomputed random walker of
+ * Andrews & Hamarneh, "Adaptable Precomputation for Random Walker Image Segmentation and
+ * Registration" (arXiv 1607.04174).
+ *
+ * Conventions for every entry point
+ * ---------------------------------
+ * - Image graphs are 2-D 4-connected or 3-D 6-connected grids with dims (X, Y, Z); voxel
+ *   (x, y, z) has linear index i = x + X * (y + Y * z).  N = X * Y * Z.
+ * - Edge id e = axis * N + i is the edge from voxel i to i + stride[axis], stride = (1, X, X*Y);
+ *   it exists when voxel i is not on the last slice along that axis.
+ * - Node-major layout: an N x k matrix stores row i (voxel i's k values) contiguously, rows
+ *   `ld` elements apart.
+ * - Pointers named *_dev are CUDA device pointers owned by the caller (e.g. from PyTorch);
+ *   *_host are host pointers.  `stream` is a cudaStream_t (NULL = legacy default stream); all
+ *   device work is enqueued on it.  The library owns only its opaque handles and the scratch
+ *   memory it keeps inside them (allocated with cudaMalloc on first use, freed with the handle).
+ * - Calls that share a handle must not run concurrently on different streams: they share the
+ *   handle's scratch memory.
+ * - Every call returns an rw_status.  On an error the outputs are unspecified and the handles
+ *   remain valid.  Errors that only the GPU can detect (a seed index out of range, a duplicate
+ *   seed, a zero pivot) are recorded in the graph handle's device status word; they are
+ *   returned by the same call when it synchronizes (see rw_solve) and otherwise by
+ *   rw_last_device_status().
+ * - No entry point falls back to the CPU.  Without a usable CUDA device every call that
+ *   enqueues GPU work returns RW_ERR_CUDA.
+ */
+#ifndef RW_H_
+#define RW_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum rw_status {
+  RW_OK = 0,
+  RW_WARN_M_CAPPED = 1,          /* adaptive m: no candidate met f <= f_max; m_max was used   */
+  RW_WARN_NOT_CONVERGED = 2,     /* eigensolver stopped at max_iter; basis returned anyway     */
+  RW_ERR_INVALID_ARG = -1,       /* bad sizes, null pointers, seed/label out of range, dups    */
+  RW_ERR_CUDA = -2,              /* a CUDA runtime call failed                                 */
+  RW_ERR_OOM = -3,               /* device allocation of scratch memory failed                 */
+  RW_ERR_NOT_CONVERGED = -4,     /* an iterative solve the caller asked to converge did not    */
+  RW_ERR_ISOLATED_NODE = -5,     /* a voxel has degree 0 (normalized Laplacian undefined)      */
+  RW_ERR_SINGULAR = -6,          /* zero pivot in a small dense factorization                  */
+  RW_ERR_TIMEOUT = -7,           /* a bounded device wait gave up                              */
+  RW_ERR_UNSUPPORTED = -9        /* valid request outside what this build implements          */
+} rw_status;
+
+/* Human-readable name of a status code (static storage). */
+const char* rw_status_str(rw_status s);
+/* Text of the last CUDA runtime error seen by this thread inside the library ("" if none). */
+const char* rw_last_error_message(void);
+/* Number of CUDA kernels this library has launched since it was loaded (all threads). */
+int64_t rw_kernel_launches(void);
+
+/* ------------------------------------------------------------------------------------------
+ * Graph (Sec. II-A, Eq. W; Sec. II-C).  w_xy = exp(-beta * (J(x)-J(y))^2) (RW_WEIGHT_SQ) or
+ * exp(-beta * |J(x)-J(y)|) (RW_WEIGHT_ABS, Eq. W as printed); D = diag(row sums of W);
+ * L = D - W; normalized L-hat = D^{-1/2} L D^{-1/2}.
+ * ---------------------------------------------------------------------------------------- */
+typedef struct rw_graph rw_graph;
+typedef struct rw_basis rw_basis;
+
+enum { RW_WEIGHT_SQ = 0, RW_WEIGHT_ABS = 1 };
+
+typedef struct rw_graph_desc {
+  int32_t ndim;         /* 2 or 3                                                           */
+  int32_t dims[3];      /* X, Y, Z (Z = 1 when ndim = 2); each >= 1, N <= 2^31 - 1           */
+  double beta;          /* >= 0                                                             */
+  int32_t weight_form;  /* RW_WEIGHT_SQ or RW_WEIGHT_ABS                                     */
+  int32_t normalized;   /* 1: use L-hat (Sec. II-C, the paper's assumption); 0: use L        */
+} rw_graph_desc;
+
+/* Builds the graph of Eq. (W) from the intensities J_dev (N floats, read only during the
+ * call's stream work; the graph keeps its own copy).  Computes the per-axis forward-edge
+ * weights, degrees and D^{-1/2}.  *out receives a new handle (free with rw_graph_free).
+ * RW_ERR_ISOLATED_NODE if normalized and some degree is 0 (this call synchronizes). */
+rw_status rw_build_graph(const rw_graph_desc* desc, const float* J_dev, void* stream,
+                         rw_graph** out);
+void rw_graph_free(rw_graph* g);
+int64_t rw_graph_num_nodes(const rw_graph* g);
+
+/* Copies the graph's per-axis weights (ndim * N floats, entry axis*N + i = weight of edge id
+ * axis*N + i, 0 where the edge does not exist) and degrees (N floats) to caller buffers.
+ * Either pointer may be NULL. */
+rw_status rw_graph_weights(const rw_graph* g, float* w_dev, float* d_dev, void* stream);
+
+/* Matrix-free Y = L-hat X (or L X when the graph is unnormalized) for an N x k node-major
+ * block (Sec. II-C, Eq. z_eig operator).  ldx, ldy >= k and multiples of 4; X_dev, Y_dev
+ * 16-byte aligned and not overlapping.  1 <= k <= 1024. */
+rw_status rw_apply_laplacian(const rw_graph* g, const float* X_dev, int64_t ldx, float* Y_dev,
+                             int64_t ldy, int32_t k, void* stream);
+
+/* ------------------------------------------------------------------------------------------
+ * Offline precomputation (Sec. II-B, Eq. L_eigs): the m smallest eigenpairs of L-hat (or L).
+ * The paper names no eigensolver; this is a block LOBPCG (blocks [X, W, P], soft locking)
+ * started by Chebyshev-filtered subspace steps on X while the worst residual exceeds 1e-3,
+ * with FP32 stencil/GEMM work and FP64 Cholesky-QR and FP64 Rayleigh-Ritz on the small
+ * projected matrices.
+ * ---------------------------------------------------------------------------------------- */
+typedef struct rw_eig_opts {
+  int32_t m;            /* eigenpairs wanted, 1 <= m <= 512                                  */
+  int32_t guard;        /* extra block columns (< 0: default max(8, m/5))                    */
+  int32_t max_iter;     /* outer iterations (<= 0: default 200)                              */
+  double tol;           /* ||L-hat q - lambda q||_2 for unit q (<= 0: default 1e-5)          */
+  int32_t cheb_degree;  /* degree of the warm-start filter (< 0: default 32; 0: no warm start) */
+  uint64_t seed;        /* seed of the random initial block                                  */
+} rw_eig_opts;
+
+typedef struct rw_eig_info {
+  int32_t iterations;
+  int32_t converged;    /* number of leading pairs meeting tol                               */
+  double max_residual;  /* over the m returned pairs                                         */
+  int32_t stencil_applies;
+} rw_eig_info;
+
+/* Computes the basis.  Returns RW_WARN_NOT_CONVERGED (basis still valid) when max_iter is
+ * reached.  Synchronizes the stream (it reads convergence flags each iteration). */
+rw_status rw_precompute(rw_graph* g, const rw_eig_opts* opts, void* stream, rw_basis** out,
+                        rw_eig_info* info);
+
+/* Wraps a caller-supplied orthonormal basis: Q_dev is N x m node-major (ld = m), lambda_host
+ * its m values (eigenvalues, or any values — Sec. III-B uses Rayleigh quotients).  Copies
+ * both; builds the 16-bit copy used by the online solve. */
+rw_status rw_basis_create(const rw_graph* g, int32_t m, const float* Q_dev,
+                          const double* lambda_host, void* stream, rw_basis** out);
+/* Copies Q (N x m, ld = m, FP32) and/or the current values (m doubles) out.  Synchronizes. */
+rw_status rw_basis_get(const rw_basis* b, float* Q_dev, double* lambda_host, void* stream);
+int32_t rw_basis_m(const rw_basis* b);
+void rw_basis_free(rw_basis* b);
+
+/* ------------------------------------------------------------------------------------------
+ * Online solve (Sec. II-B Eqs. Fs, U_lin_comb; Sec. II-C normalized form; Sec. III-A-1 choice
+ * of m).  With Lambda_gamma = (Lambda + gamma I)^{-1}, X = B Q_n, Z = Q_n^T P_n:
+ *   (I - X Lambda_gamma Q_s^T) F_s = L_s U_s + gamma (U_s + X Lambda_gamma Z)      Eq. (Fs)
+ *   U_n = Q_n Lambda_gamma (Q_s^T F_s + gamma Z)                           Eq. (U_lin_comb)
+ * solved through the equivalent m x m system (Lambda_gamma^{-1} - Q_s^T X) y = Q_s^T rhs,
+ * C = y + gamma Lambda_gamma Z, U_n = Q_n C (Woodbury form of Eq. Fs).  Then refine_steps
+ * damped-Jacobi steps on Eq. (rw_eq) and hard labels = argmax (ties -> lowest label).
+ * ---------------------------------------------------------------------------------------- */
+enum { RW_REFINE_JACOBI = 0, RW_REFINE_PCG = 1 };
+enum { RW_BASIS_F16 = 0, RW_BASIS_BF16 = 1, RW_BASIS_F32 = 2 };
+#define RW_MAX_LABELS 16
+
+typedef struct rw_solve_opts {
+  double gamma;          /* prior weight of Eq. (rw_energy); > 0 (gamma = 0 unsupported)     */
+  int32_t m;             /* eigenvectors used; 0 = adaptive (Sec. III-A-1), else <= basis m  */
+  int32_t m_step;        /* adaptive candidates m_step, 2 m_step, ..., m_max (<= 0: 10)      */
+  double eps;            /* adaptive accuracy, f_max = S eps^2 (<= 0: 0.1, the paper's)     */
+  int32_t refine_steps;  /* refinement steps after the projection (>= 0)                     */
+  int32_t refine_mode;   /* RW_REFINE_JACOBI (damped, omega) or RW_REFINE_PCG                */
+  double omega;          /* damping of the Jacobi steps, (0, 1] (<= 0: 0.8)                  */
+  int32_t basis_format;  /* storage read by the two N x m passes: RW_BASIS_F16 (scaled FP16,
+                            default), RW_BASIS_BF16, RW_BASIS_F32                            */
+  int32_t prior_mode;    /* 0: Gaussian fit to the seed intensities (Sec. IV-A);
+                            1: caller priors in priors_dev (N x n_labels, rows sum to 1)     */
+  int32_t record_phases; /* 1: record CUDA events between the solve's phases on `stream` and
+                            report their durations in rw_solve_info.phase_ms (needs info)    */
+} rw_solve_opts;
+
+/* Phases of one online solve, in order (indices into rw_solve_info.phase_ms). */
+enum {
+  RW_PHASE_SEEDS = 0,     /* seed scatter/validation, Gaussian fit, hat-space priors          */
+  RW_PHASE_GATHER = 1,    /* Q_s, X = B Q_n, seed-side products Q_s^T X, Q_s^T r, Q_s^T Q_s    */
+  RW_PHASE_ADAPT = 2,     /* choice of m (Eq. alpha_1)                                        */
+  RW_PHASE_PROJECT = 3,   /* Z = Q_n^T P_n (one pass over the 16-bit basis)                   */
+  RW_PHASE_SMALL = 4,     /* m x m system of Eq. (Fs) in Woodbury form                        */
+  RW_PHASE_BACK = 5,      /* U_n = Q_n C (second pass over the basis)                         */
+  RW_PHASE_REFINE = 6,    /* refinement steps, output, hard labels                            */
+  RW_NUM_PHASES = 7
+};
+
+typedef struct rw_solve_info {
+  int32_t m_used;
+  int32_t capped;                 /* adaptive m hit m_max without meeting f_max             */
+  int32_t device_status;          /* rw_status recorded on the device during this solve     */
+  int32_t pad_;
+  double f_max;                   /* S eps^2                                                 */
+  double f[RW_MAX_LABELS];        /* f(u_s^k) at m_used (adaptive mode), else 0              */
+  double mu[RW_MAX_LABELS];       /* Gaussian prior means (prior_mode 0)                     */
+  double sigma[RW_MAX_LABELS];    /* Gaussian prior std devs (prior_mode 0)                  */
+  float phase_ms[8];              /* per-phase GPU time (record_phases = 1), else 0          */
+} rw_solve_info;
+
+/* seed_idx_dev, seed_lab_dev: S int32 each (voxel index in [0, N), label in [0, n_labels));
+ * seeds must be distinct voxels; every label needs >= 1 seed in prior_mode 0.
+ * prob_dev: N x n_labels FP32, node-major, ld = n_labels (caller-owned output).
+ * labels_dev: N uint8 hard labels, or NULL.  info: host struct or NULL.
+ * 1 <= S <= 65536, 1 <= n_labels <= RW_MAX_LABELS.  Asynchronous when info == NULL: device-side
+ * errors are then reported by rw_last_device_status().  With info != NULL the call
+ * synchronizes the stream and returns the device status. */
+rw_status rw_solve(const rw_graph* g, const rw_basis* b, const int32_t* seed_idx_dev,
+                   const int32_t* seed_lab_dev, int32_t S, int32_t n_labels,
+                   const float* priors_dev, const rw_solve_opts* opts, float* prob_dev,
+                   uint8_t* labels_dev, rw_solve_info* info, void* stream);
+
+/* Same solve with HOST buffers: copies the seeds (and priors) in and prob/labels out on
+ * `stream` (pinned host memory makes the copies asynchronous), then synchronizes. */
+rw_status rw_solve_host(const rw_graph* g, const rw_basis* b, const int32_t* seed_idx_host,
+                        const int32_t* seed_lab_host, int32_t S, int32_t n_labels,
+                        const float* priors_host, const rw_solve_opts* opts, float* prob_host,
+                        uint8_t* labels_host, rw_solve_info* info, void* stream);
+
+/* Reads (and clears) the graph's device status word.  Synchronizes the stream. */
+rw_status rw_last_device_status(const rw_graph* g, void* stream);
+
+/* Basic RW on the GPU (the paper's "basic RW", Eq. rw_eq, normalized form of Sec. II-C), by
+ * Jacobi-preconditioned CG from a zero start, all labels at once: the comparison solver.
+ * Runs exactly `iters` iterations when tol <= 0, else stops when every column's relative
+ * residual is <= tol (at most iters).  Same seed/prior/output conventions as rw_solve.
+ * *iters_done (host, may be NULL) receives the iterations run; synchronizes if non-NULL. */
+rw_status rw_solve_pcg(const rw_graph* g, const int32_t* seed_idx_dev,
+                       const int32_t* seed_lab_dev, int32_t S, int32_t n_labels,
+                       const float* priors_dev, double gamma, int32_t prior_mode,
+                       int32_t iters, double tol, float* prob_dev, uint8_t* labels_dev,
+                       int32_t* iters_done, void* stream);
+
+/* ------------------------------------------------------------------------------------------
+ * Updates (Sec. III-B, Eq. z_ray; Sec. III-C).  The columns of Q are kept and their values
+ * become lambda-hat_i = q_i^T L-hat_new q_i, evaluated as the edge sum
+ * sum_e w_e (q_i(a) d_a^{-1/2} - q_i(b) d_b^{-1/2})^2.
+ * ---------------------------------------------------------------------------------------- */
+enum { RW_UPDATE_BETA = 0, RW_UPDATE_EDGES = 1, RW_UPDATE_ROI = 2 };
+
+typedef struct rw_weight_update {
+  int32_t kind;               /* RW_UPDATE_*                                                 */
+  int32_t pad_;
+  double beta;                /* BETA: new beta for every edge; ROI: beta inside the box      */
+  int32_t roi_lo[3];          /* ROI: half-open box [lo, hi) per axis; edges with both ends   */
+  int32_t roi_hi[3];          /*      inside are recomputed from Eq. (W)                      */
+  const int64_t* edge_ids_dev;/* EDGES: n_edges distinct edge ids                             */
+  const float* edge_w_dev;    /* EDGES: their new weights (>= 0)                              */
+  int64_t n_edges;
+} rw_weight_update;
+
+/* Mutates the graph's weights and the basis values in place (basis must belong to g).  The
+ * ROI and EDGES kinds update the values incrementally from the edges whose contribution
+ * changed.  RW_ERR_ISOLATED_NODE if a degree becomes 0.  Synchronizes. */
+rw_status rw_update_weights(rw_graph* g, rw_basis* b, const rw_weight_update* u, void* stream);
+
+enum { RW_TOPO_REMOVE_EDGES = 0, RW_TOPO_AGGREGATE = 1 };
+
+typedef struct rw_topology_update {
+  int32_t kind;                 /* RW_TOPO_*                                                 */
+  int32_t naive;                /* AGGREGATE: 1 = Eq. (q_agg_1), 0 = Eq. (q_agg_2)           */
+  const int64_t* edge_ids_dev;  /* REMOVE_EDGES: ids of edges to remove (w_e := 0)           */
+  int64_t n_edges;
+  int64_t n_bar;                /* AGGREGATE: number of super-vertices                       */
+  const int32_t* eta_rowptr_dev;/* AGGREGATE: eta (N x n_bar) CSR, rows sum to 1, columns   */
+  const int32_t* eta_col_dev;   /*   sorted within each row                                  */
+  const float* eta_val_dev;
+  const float* etabar_val_dev;  /* eta-bar on eta's sparsity pattern (columns sum to 1), or
+                                   NULL: eta with its columns normalized                      */
+} rw_topology_update;
+
+/* REMOVE_EDGES: same vertex set, handled like a weight update (Sec. III-B), g and b mutated.
+ * AGGREGATE (Sec. III-C): returns a new general (CSR) graph on the super-vertices with
+ * L-bar = eta^T L eta and a new basis Q-bar (aggregated columns, Gram-Schmidt-orthonormalized
+ * through FP64 Cholesky-QR, nearly dependent columns dropped) with Ncut values on the new
+ * graph.  g and b are unchanged.  Synchronizes. */
+rw_status rw_update_topology(rw_graph* g, rw_basis* b, const rw_topology_update* u,
+                             void* stream, rw_graph** agg_graph_out, rw_basis** agg_basis_out);
+
+/* ------------------------------------------------------------------------------------------
+ * Gradients (not in the paper; derived from Eq. rw_eq and Eq. W).  For a loss on U with
+ * dloss_dU_dev = d loss / d U (N x n_labels node-major; seeded rows ignored):
+ *   exact path: adjoint A lambda = dloss/dU_n (A = L_n + gamma D_n) by Jacobi-PCG to rel_tol,
+ *   d loss / d w_e = -sum_k [(lam_a - lam_b)(u_a - u_b) + gamma (lam_a (u_a - p_a)
+ *                            + lam_b (u_b - p_b))]   (second term only when normalized),
+ *   d loss / d beta = sum_e (d loss / d w_e) (d w_e / d beta).
+ * U_dev must be the converged exact solution (e.g. rw_solve_pcg with a tight tol) and
+ * priors_dev the priors it used (N x n_labels, e.g. from rw_solve_priors).
+ * grad_w_dev: ndim * N floats in edge-id layout (0 where no edge).  grad_beta_host: 1 double.
+ * Synchronizes.
+ * ---------------------------------------------------------------------------------------- */
+rw_status rw_grad_exact(const rw_graph* g, const int32_t* seed_idx_dev,
+                        const int32_t* seed_lab_dev, int32_t S, int32_t n_labels,
+                        const float* priors_dev, double gamma, const float* U_dev,
+                        const float* dloss_dU_dev, double rel_tol, int32_t max_iter,
+                        float* grad_w_dev, double* grad_beta_host, void* stream);
+
+/* Writes the Gaussian-fit priors of Sec. IV-A (N x n_labels, node-major) for the seeds. */
+rw_status rw_solve_priors(const rw_graph* g, const int32_t* seed_idx_dev,
+                          const int32_t* seed_lab_dev, int32_t S, int32_t n_labels,
+                          float* priors_dev, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RW_H_ */

@@ -1,0 +1,235 @@
+"""GB300 (sm_103a) precomputed random walker: thin Python binding of the C ABI in include/rw.h.
+
+Each function here has the name of the C entry point it calls and only marshals arguments:
+device buffers are PyTorch CUDA tensors (passed by pointer), host buffers NumPy arrays, the
+stream is the current PyTorch stream unless given.  Handles are opaque integers.  A negative
+status raises RWError; there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+
+from . import abi
+from .abi import *  # noqa: F401,F403  (status codes and enums)
+
+
+class RWError(RuntimeError):
+    def __init__(self, status, what):
+        msg = abi.lib().rw_status_str(status).decode()
+        detail = abi.lib().rw_last_error_message().decode()
+        super().__init__(f"{what}: {msg}" + (f" ({detail})" if detail else ""))
+        self.status = status
+
+
+def _check(s, what):
+    if s < 0:
+        raise RWError(s, what)
+    return s
+
+
+def _p(x):
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("host arrays must be C-contiguous")
+        return x.ctypes.data
+    return x.data_ptr()  # torch tensor
+
+
+def _stream(stream):
+    if stream is not None:
+        return stream if isinstance(stream, int) else stream.cuda_stream
+    import torch
+    return torch.cuda.current_stream().cuda_stream
+
+
+def _ld(t):
+    return t.stride(0) if t.dim() == 2 else t.shape[-1]
+
+
+def rw_status_str(s):
+    return abi.lib().rw_status_str(s).decode()
+
+
+def rw_last_error_message():
+    return abi.lib().rw_last_error_message().decode()
+
+
+def rw_kernel_launches():
+    return abi.lib().rw_kernel_launches()
+
+
+def rw_build_graph(J, dims, beta, weight_form=abi.RW_WEIGHT_SQ, normalized=True, stream=None):
+    d = abi.rw_graph_desc()
+    d.ndim = len(dims)
+    for i in range(3):
+        d.dims[i] = int(dims[i]) if i < len(dims) else 1
+    d.beta = float(beta)
+    d.weight_form = int(weight_form)
+    d.normalized = 1 if normalized else 0
+    h = C.c_void_p()
+    _check(abi.lib().rw_build_graph(C.byref(d), _p(J), _stream(stream), C.byref(h)),
+           "rw_build_graph")
+    return h.value
+
+
+def rw_graph_free(g):
+    abi.lib().rw_graph_free(g)
+
+
+def rw_graph_num_nodes(g):
+    return abi.lib().rw_graph_num_nodes(g)
+
+
+def rw_graph_weights(g, w=None, d=None, stream=None):
+    return _check(abi.lib().rw_graph_weights(g, _p(w), _p(d), _stream(stream)), "rw_graph_weights")
+
+
+def rw_apply_laplacian(g, X, Y, k=None, stream=None):
+    k = X.shape[1] if k is None else k
+    return _check(abi.lib().rw_apply_laplacian(g, _p(X), _ld(X), _p(Y), _ld(Y), k,
+                                               _stream(stream)), "rw_apply_laplacian")
+
+
+def rw_precompute(g, m, guard=-1, max_iter=0, tol=0.0, cheb_degree=-1, seed=0, stream=None):
+    o = abi.rw_eig_opts(m=m, guard=guard, max_iter=max_iter, tol=tol, cheb_degree=cheb_degree,
+                        seed=seed)
+    info = abi.rw_eig_info()
+    h = C.c_void_p()
+    s = _check(abi.lib().rw_precompute(g, C.byref(o), _stream(stream), C.byref(h), C.byref(info)),
+               "rw_precompute")
+    return h.value, dict(status=s, iterations=info.iterations, converged=info.converged,
+                         max_residual=info.max_residual, stencil_applies=info.stencil_applies)
+
+
+def rw_basis_create(g, Q, lam, stream=None):
+    lam = np.ascontiguousarray(lam, dtype=np.float64)
+    h = C.c_void_p()
+    _check(abi.lib().rw_basis_create(g, Q.shape[1], _p(Q),
+                                     lam.ctypes.data_as(C.POINTER(C.c_double)), _stream(stream),
+                                     C.byref(h)), "rw_basis_create")
+    return h.value
+
+
+def rw_basis_m(b):
+    return abi.lib().rw_basis_m(b)
+
+
+def rw_basis_get(b, Q=None, stream=None):
+    lam = np.zeros(rw_basis_m(b))
+    _check(abi.lib().rw_basis_get(b, _p(Q), lam.ctypes.data_as(C.POINTER(C.c_double)),
+                                  _stream(stream)), "rw_basis_get")
+    return lam
+
+
+def rw_basis_free(b):
+    abi.lib().rw_basis_free(b)
+
+
+def _solve_opts(gamma, m, m_step, eps, refine_steps, refine_mode, omega, basis_format,
+                prior_mode, record_phases=0):
+    return abi.rw_solve_opts(gamma=gamma, m=m, m_step=m_step, eps=eps, refine_steps=refine_steps,
+                             refine_mode=refine_mode, omega=omega, basis_format=basis_format,
+                             prior_mode=prior_mode, record_phases=record_phases)
+
+
+def _info_dict(info, n_labels):
+    return dict(m_used=info.m_used, capped=info.capped, device_status=info.device_status,
+                f_max=info.f_max, f=list(info.f)[:n_labels], mu=list(info.mu)[:n_labels],
+                sigma=list(info.sigma)[:n_labels],
+                phase_ms=dict(zip(abi.RW_PHASES, list(info.phase_ms)[:len(abi.RW_PHASES)])))
+
+
+def rw_solve(g, b, seed_idx, seed_lab, n_labels, prob, labels=None, priors=None, gamma=1e-3,
+             m=0, m_step=10, eps=0.1, refine_steps=3, refine_mode=abi.RW_REFINE_JACOBI,
+             omega=0.8, basis_format=abi.RW_BASIS_F16, prior_mode=0, want_info=True,
+             record_phases=False, stream=None):
+    o = _solve_opts(gamma, m, m_step, eps, refine_steps, refine_mode, omega, basis_format,
+                    prior_mode, 1 if record_phases else 0)
+    info = abi.rw_solve_info()
+    s = _check(abi.lib().rw_solve(g, b, _p(seed_idx), _p(seed_lab), len(seed_idx), n_labels,
+                                  _p(priors), C.byref(o), _p(prob), _p(labels),
+                                  C.byref(info) if want_info else None, _stream(stream)),
+               "rw_solve")
+    return s, (_info_dict(info, n_labels) if want_info else None)
+
+
+def rw_solve_host(g, b, seed_idx, seed_lab, n_labels, prob, labels=None, priors=None, gamma=1e-3,
+                  m=0, m_step=10, eps=0.1, refine_steps=3, refine_mode=abi.RW_REFINE_JACOBI,
+                  omega=0.8, basis_format=abi.RW_BASIS_F16, prior_mode=0, want_info=False,
+                  stream=None):
+    o = _solve_opts(gamma, m, m_step, eps, refine_steps, refine_mode, omega, basis_format,
+                    prior_mode)
+    info = abi.rw_solve_info()
+    s = _check(abi.lib().rw_solve_host(g, b, _p(seed_idx), _p(seed_lab), len(seed_idx),
+                                       n_labels, _p(priors), C.byref(o), _p(prob), _p(labels),
+                                       C.byref(info) if want_info else None, _stream(stream)),
+               "rw_solve_host")
+    return s, (_info_dict(info, n_labels) if want_info else None)
+
+
+def rw_last_device_status(g, stream=None):
+    return abi.lib().rw_last_device_status(g, _stream(stream))
+
+
+def rw_solve_pcg(g, seed_idx, seed_lab, n_labels, prob, labels=None, priors=None, gamma=1e-3,
+                 prior_mode=0, iters=1000, tol=0.0, want_iters=True, stream=None):
+    it = C.c_int32(0)
+    _check(abi.lib().rw_solve_pcg(g, _p(seed_idx), _p(seed_lab), len(seed_idx), n_labels,
+                                  _p(priors), gamma, prior_mode, iters, tol, _p(prob), _p(labels),
+                                  C.byref(it) if want_iters else None, _stream(stream)),
+           "rw_solve_pcg")
+    return it.value if want_iters else None
+
+
+def rw_update_weights(g, b, kind, beta=0.0, roi_lo=(0, 0, 0), roi_hi=(1, 1, 1), edge_ids=None,
+                      edge_w=None, stream=None):
+    u = abi.rw_weight_update()
+    u.kind = kind
+    u.beta = beta
+    for i in range(3):
+        u.roi_lo[i] = roi_lo[i] if i < len(roi_lo) else 0
+        u.roi_hi[i] = roi_hi[i] if i < len(roi_hi) else 1
+    u.edge_ids_dev = _p(edge_ids)
+    u.edge_w_dev = _p(edge_w)
+    u.n_edges = 0 if edge_ids is None else len(edge_ids)
+    return _check(abi.lib().rw_update_weights(g, b, C.byref(u), _stream(stream)),
+                  "rw_update_weights")
+
+
+def rw_update_topology(g, b, kind, edge_ids=None, n_bar=0, eta_rowptr=None, eta_col=None,
+                       eta_val=None, etabar_val=None, naive=False, stream=None):
+    u = abi.rw_topology_update()
+    u.kind = kind
+    u.naive = 1 if naive else 0
+    u.edge_ids_dev = _p(edge_ids)
+    u.n_edges = 0 if edge_ids is None else len(edge_ids)
+    u.n_bar = n_bar
+    u.eta_rowptr_dev = _p(eta_rowptr)
+    u.eta_col_dev = _p(eta_col)
+    u.eta_val_dev = _p(eta_val)
+    u.etabar_val_dev = _p(etabar_val)
+    ga, ba = C.c_void_p(), C.c_void_p()
+    s = _check(abi.lib().rw_update_topology(g, b, C.byref(u), _stream(stream), C.byref(ga),
+                                            C.byref(ba)), "rw_update_topology")
+    return s, ga.value, ba.value
+
+
+def rw_grad_exact(g, seed_idx, seed_lab, n_labels, priors, gamma, U, dloss_dU, grad_w,
+                  rel_tol=1e-7, max_iter=20000, stream=None):
+    gb = C.c_double(0.0)
+    _check(abi.lib().rw_grad_exact(g, _p(seed_idx), _p(seed_lab), len(seed_idx), n_labels,
+                                   _p(priors), gamma, _p(U), _p(dloss_dU), rel_tol, max_iter,
+                                   _p(grad_w), C.byref(gb), _stream(stream)), "rw_grad_exact")
+    return gb.value
+
+
+def rw_solve_priors(g, seed_idx, seed_lab, n_labels, priors, stream=None):
+    return _check(abi.lib().rw_solve_priors(g, _p(seed_idx), _p(seed_lab), len(seed_idx),
+                                            n_labels, _p(priors), _stream(stream)),
+                  "rw_solve_priors")

@@ -1,0 +1,157 @@
+// Internal definitions shared by the CUDA translation units of the random-walker library.
+// Nothing here is part of the C ABI (include/rw.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include "../../include/rw.h"
+
+#define RW_CHECK_CUDA(call)                                                     \
+  do {                                                                          \
+    cudaError_t e_ = (call);                                                    \
+    if (e_ != cudaSuccess) {                                                    \
+      rw_set_last_cuda_error(e_, #call, __FILE__, __LINE__);                    \
+      return (e_ == cudaErrorMemoryAllocation) ? RW_ERR_OOM : RW_ERR_CUDA;      \
+    }                                                                           \
+  } while (0)
+
+#define RW_TRY(expr)                        \
+  do {                                      \
+    rw_status s_ = (expr);                  \
+    if (s_ < 0) return s_;                  \
+  } while (0)
+
+void rw_count_launch();
+#define RW_LAUNCH_CHECK()  \
+  do {                     \
+    rw_count_launch();     \
+    RW_CHECK_CUDA(cudaGetLastError()); \
+  } while (0)
+
+void rw_set_last_cuda_error(cudaError_t e, const char* what, const char* file, int line);
+
+// Device status word bits (ORed by kernels, read by the host).
+enum : int {
+  RW_DEV_BAD_SEED = 1,       // seed index out of range or label out of range
+  RW_DEV_DUP_SEED = 2,       // two seeds on one voxel
+  RW_DEV_ISOLATED = 4,       // degree 0 with the normalized Laplacian
+  RW_DEV_SINGULAR = 8,       // zero pivot in a small dense factorization
+  RW_DEV_EMPTY_LABEL = 16,   // a label without seeds (Gaussian priors need one)
+  RW_DEV_NONFINITE = 32      // NaN / Inf in an input
+};
+rw_status rw_status_from_device_bits(int bits);
+
+// A growable device buffer owned by a handle.  grow() may reallocate (synchronous).
+struct DevBuf {
+  void* p = nullptr;
+  size_t cap = 0;
+  rw_status grow(size_t bytes);
+  void release();
+  template <class T> T* as() const { return reinterpret_cast<T*>(p); }
+};
+
+struct PinnedBuf {
+  void* p = nullptr;
+  size_t cap = 0;
+  rw_status grow(size_t bytes);
+  void release();
+  template <class T> T* as() const { return reinterpret_cast<T*>(p); }
+};
+
+enum { RW_GRAPH_GRID = 0, RW_GRAPH_CSR = 1 };
+
+struct SolveWorkspace {
+  DevBuf seedlab;   // int8 [N]: -1 unseeded, else label
+  DevBuf small;     // small per-solve arrays (stats, Q_s, X, products, Z, C, ...)
+  DevBuf xhat[2];   // refinement iterates, N x lpad FP32
+  DevBuf phat;      // hat-space priors, N x lpad FP32
+  DevBuf pcg;       // PCG vectors
+  DevBuf stage;     // device staging of the host-buffer entry point
+  PinnedBuf host;   // info readback
+  cudaEvent_t ev[8] = {};  // phase timing events (created on first use)
+  int64_t small_cap_S = 0, small_cap_m = 0;
+};
+
+struct rw_graph {
+  int kind = RW_GRAPH_GRID;
+  int ndim = 2;
+  int dims[3] = {1, 1, 1};
+  int64_t N = 0;
+  int64_t stride[3] = {1, 1, 1};
+  double beta = 0.0;
+  int form = RW_WEIGHT_SQ;
+  int normalized = 1;
+  // grid graphs: per-axis forward-edge arrays, entry axis*N + i
+  float* J = nullptr;    // N intensities
+  float* w = nullptr;    // ndim*N weights
+  float* cw = nullptr;   // ndim*N operator coefficients: w * s_a * s_b (normalized) or w
+  // csr graphs (aggregates): symmetric, no diagonal
+  int32_t* rowptr = nullptr;
+  int32_t* col = nullptr;
+  float* wcsr = nullptr;  // weights
+  float* ccsr = nullptr;  // operator coefficients
+  int64_t nnz = 0;
+  // per-node
+  float* d = nullptr;     // degree
+  float* s = nullptr;     // d^{-1/2} (normalized) or 1
+  float* sq = nullptr;    // d^{1/2} (normalized) or 1
+  int* status = nullptr;  // device status word
+  double dsum = 0.0;      // sum of degrees (1^T D 1)
+  SolveWorkspace ws;
+  DevBuf upd;             // update scratch
+};
+
+struct rw_basis {
+  int64_t N = 0;
+  int m = 0;
+  int ld32 = 0;           // row pitch of Q32 (multiple of 4)
+  int ld16 = 0;           // row pitch of the 16-bit copies (multiple of 8)
+  float* Q32 = nullptr;   // N x ld32
+  __half* Q16 = nullptr;  // N x ld16, scaled by qscale (power of two)
+  __nv_bfloat16* Qbf = nullptr;  // N x ld16, unscaled, built on first use
+  float qscale = 1.f;
+  double* lam = nullptr;  // m values on the device
+  double* lam_host = nullptr;
+  const rw_graph* owner = nullptr;
+};
+
+// ---- helpers shared across translation units -----------------------------------------
+static inline int64_t rw_round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
+static inline unsigned rw_blocks(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+static inline cudaStream_t rw_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+extern int g_rw_num_sms;
+rw_status rw_device_init();
+
+// graph.cu
+rw_status rw_stencil_apply(const rw_graph* g, const float* X, int64_t ldx, float* Y,
+                           int64_t ldy, int k, float alpha, float beta, const float* Z,
+                           int64_t ldz, float gamma, cudaStream_t st);
+rw_status rw_graph_coeffs(rw_graph* g, cudaStream_t st);
+rw_status rw_graph_degree_sum(rw_graph* g, cudaStream_t st);  // sets g->dsum, synchronizes
+rw_status rw_graph_reserve_scratch(rw_graph* g);
+
+// dense.cu (small / tall-skinny dense helpers)
+// G (p x q, row-major, ldg, FP64) = (accumulate ? G : 0) + A^T B, A: N x p (lda), B: N x q (ldb)
+rw_status rw_gram(const float* A, int64_t lda, const float* B, int64_t ldb, int64_t N, int p,
+                  int q, double* G, int ldg, bool accumulate, cudaStream_t st);
+// Y (N x p) = alpha * A (N x q) * C (q x p, row-major FP32, ldc) + beta * Y
+rw_status rw_gemm_tall(const float* A, int64_t lda, const float* C, int ldc, int64_t N, int q,
+                       int p, float alpha, float beta, float* Y, int64_t ldy, cudaStream_t st);
+// in place: A (n x n, row-major FP64) := upper-triangular R with R^T R = A + shift*I; returns
+// via flag device word when a pivot is not positive
+rw_status rw_cholesky_upper(double* A, int n, double shift, int* flag, cudaStream_t st);
+// Rinv (n x n FP32 row-major) = inverse of the upper-triangular R (FP64)
+rw_status rw_tri_inverse_upper(const double* R, int n, float* Rinv, cudaStream_t st);
+// symmetric eigensolver (cyclic Jacobi, FP64): A (n x n) destroyed; w ascending; V columns
+rw_status rw_sym_eig(double* A, int n, double* w, double* V, double* work, cudaStream_t st);
+size_t rw_sym_eig_work_bytes(int n);
+rw_status rw_copy_cols(const float* src, int64_t lds, float* dst, int64_t ldd, int64_t N,
+                       const int* cols, int ncols, cudaStream_t st);
+rw_status rw_f64_to_f32(const double* a, float* b, int64_t n, cudaStream_t st);
+
+// update.cu: edge-sum Rayleigh quotients of every basis column under g -> b->lam (synchronizes)
+rw_status rw_basis_rayleigh(const rw_graph* g, rw_basis* b, cudaStream_t st);

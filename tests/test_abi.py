@@ -1,0 +1,82 @@
+"""CPU checks of the C ABI: the library builds, loads, exports every entry point that
+include/rw.h declares, and the ctypes structs match the C layouts (sizes and offsets from a
+gcc-compiled probe).  No compute calls: there is no GPU here."""
+import ctypes as C
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "rw.h")
+
+
+def _declared():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(rw_[a-z_0-9]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1607_04174_gb300 import abi, build
+    build.build()
+    return abi.lib()
+
+
+def test_every_declared_entry_point_is_exported(lib):
+    names = _declared()
+    assert len(names) >= 20
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_covers_every_entry_point():
+    from paper_1607_04174_gb300 import abi
+    import paper_1607_04174_gb300 as rw
+    for n in _declared():
+        assert n in abi.PROTOTYPES, n
+        assert hasattr(rw, n), n
+
+
+def test_status_strings(lib):
+    lib.rw_status_str.restype = C.c_char_p
+    assert lib.rw_status_str(0) == b"RW_OK"
+    assert lib.rw_status_str(-1) == b"RW_ERR_INVALID_ARG"
+    assert lib.rw_status_str(-9) == b"RW_ERR_UNSUPPORTED"
+    assert lib.rw_status_str(12345) == b"RW_UNKNOWN_STATUS"
+
+
+def test_struct_layouts_match_c(tmp_path):
+    from paper_1607_04174_gb300 import abi
+    structs = {
+        "rw_graph_desc": ["ndim", "dims", "beta", "weight_form", "normalized"],
+        "rw_eig_opts": ["m", "guard", "max_iter", "tol", "cheb_degree", "seed"],
+        "rw_eig_info": ["iterations", "converged", "max_residual", "stencil_applies"],
+        "rw_solve_opts": ["gamma", "m", "m_step", "eps", "refine_steps", "refine_mode", "omega",
+                          "basis_format", "prior_mode", "record_phases"],
+        "rw_solve_info": ["m_used", "capped", "device_status", "f_max", "f", "mu", "sigma",
+                          "phase_ms"],
+        "rw_weight_update": ["kind", "beta", "roi_lo", "roi_hi", "edge_ids_dev", "edge_w_dev",
+                             "n_edges"],
+        "rw_topology_update": ["kind", "naive", "edge_ids_dev", "n_edges", "n_bar",
+                               "eta_rowptr_dev", "eta_col_dev", "eta_val_dev", "etabar_val_dev"],
+    }
+    lines = ['#include <stdio.h>', '#include <stddef.h>', f'#include "{HEADER}"', "int main(){"]
+    for s, fields in structs.items():
+        lines.append(f'printf("{s} %zu\\n", sizeof({s}));')
+        for f in fields:
+            lines.append(f'printf("{s}.{f} %zu\\n", offsetof({s}, {f}));')
+    lines.append("return 0;}")
+    src = tmp_path / "probe.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "probe"
+    subprocess.run(["gcc", "-std=c11", str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout
+    got = dict(line.split() for line in out.strip().splitlines())
+    for s, fields in structs.items():
+        cls = getattr(abi, s)
+        assert int(got[s]) == C.sizeof(cls), s
+        for f in fields:
+            assert int(got[f"{s}.{f}"]) == getattr(cls, f).offset, f"{s}.{f}"
