@@ -11,7 +11,8 @@ namespace cg = cooperative_groups;
 
 // ---------------------------------------------------------------------------------------
 // G += A^T B.  A: N x p, B: N x q (node-major FP32).  64 x 64 output tile per CTA, the N rows
-// split across gridDim.z; FP32 partial sums within a CTA, FP64 atomic accumulation across.
+// split across gridDim.z; FP32 partial sums over 256 rows, flushed into FP64 accumulators, and
+// FP64 atomic accumulation across CTAs.
 // ---------------------------------------------------------------------------------------
 namespace {
 constexpr int GT = 64, GK = 32;
@@ -27,7 +28,16 @@ k_gram(const float* __restrict__ A, int64_t lda, const float* __restrict__ B, in
   const int64_t r1 = min(N, r0 + rows_per_cta);
   const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
   float acc[4][4] = {};
+  double accd[4][4] = {};
+  int since_flush = 0;
   for (int64_t k0 = r0; k0 < r1; k0 += GK) {
+    if (++since_flush == 8) {  // 256 rows
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) { accd[u][v] += acc[u][v]; acc[u][v] = 0.f; }
+      since_flush = 0;
+    }
     for (int e = threadIdx.x; e < GK * GT; e += 256) {
       int kk = e / GT, ii = e % GT;
       int64_t r = k0 + kk;
@@ -53,7 +63,7 @@ k_gram(const float* __restrict__ A, int64_t lda, const float* __restrict__ B, in
 #pragma unroll
     for (int v = 0; v < 4; ++v) {
       int i = i0 + ty * 4 + u, j = j0 + tx * 4 + v;
-      if (i < p && j < q) atomicAdd(&G[(int64_t)i * ldg + j], (double)acc[u][v]);
+      if (i < p && j < q) atomicAdd(&G[(int64_t)i * ldg + j], accd[u][v] + (double)acc[u][v]);
     }
 }
 
@@ -154,13 +164,13 @@ __global__ void __launch_bounds__(1024) k_cholesky_upper(double* A, int n, doubl
   __syncthreads();
   double scale = 0.0;
   for (int i = 0; i < n; ++i) scale = fmax(scale, fabs(A[(int64_t)i * n + i]));
-  const double tiny = (scale > 0 ? scale : 1.0) * 1e-300;
+  const double floor_piv = (scale > 0 ? scale : 1.0) * 1e-12;
   for (int k = 0; k < n; ++k) {
     __syncthreads();
     double piv = A[(int64_t)k * n + k];
     if (!(piv > 0.0)) {
       if (threadIdx.x == 0 && flag) *flag = 1;
-      piv = fmax(tiny, fabs(scale) * 1e-30);
+      piv = floor_piv;  // keeps R finite; the caller sees the flag
     }
     const double r = sqrt(piv);
     __syncthreads();

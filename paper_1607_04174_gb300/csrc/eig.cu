@@ -1,24 +1,28 @@
 // Offline precomputation (Sec. II-B, Eq. L_eigs): the m smallest eigenpairs of L-hat (or L),
 // and the basis handle used online.
 //
-// The paper names no eigensolver.  This is block LOBPCG with a Chebyshev-filtered warm start:
-// * while the largest residual of the wanted columns exceeds 1e-3, the block X (m + guard
-//   columns) is replaced by p(Op) X, p the scaled Chebyshev polynomial that damps the spectrum
-//   above the block's largest Ritz value, followed by Cholesky-QR and an nb x nb Rayleigh-Ritz
-//   (filtered subspace iteration);
-// * then LOBPCG iterations on the basis [X | W | P]: W the residuals of the columns not yet
-//   converged (soft locking), P the previous update directions, [W P] orthogonalized against X
-//   (block Gram-Schmidt, two passes) and orthonormalized by shifted Cholesky-QR (two passes,
-//   FP64 Cholesky); the projected matrix S^T (Op S) is formed in FP64 and diagonalized by the
-//   FP64 Jacobi solver.
-// Using the Chebyshev polynomial as a preconditioner of W instead (an indefinite operator on
-// the damped interval) made LOBPCG stagnate at residuals near 1e-2 in FP64 experiments, while
-// the warm start above converged in a handful of outer iterations.  Bulk work (stencil, Gram,
-// tall GEMMs) runs in FP32 on node-major N x k blocks.
+// The paper names no eigensolver.  This is a block solver with two kinds of outer step on the
+// block X (m + guard columns):
+// * a Chebyshev-filtered subspace step: X <- p(Op) X, p the scaled Chebyshev polynomial that
+//   damps the spectrum above the block's largest Ritz value, then Cholesky-QR and an nb x nb
+//   Rayleigh-Ritz;
+// * an LOBPCG step on the basis [X | W | P]: W the residuals of the columns not yet converged
+//   (soft locking), P the previous update directions, [W P] orthogonalized against X (block
+//   Gram-Schmidt, two passes) and orthonormalized by shifted Cholesky-QR (two passes, FP64
+//   Cholesky); the projected matrix S^T (Op S) is formed in FP64 and diagonalized by the FP64
+//   Jacobi solver.
+// Filtered steps run while they keep reducing the worst residual of the wanted columns (by at
+// least 30% per step); LOBPCG steps take over when they stall.  In FP32-storage experiments
+// (512^2 and 256^2 four-region images) the filtered steps alone reached 1e-5 in about a dozen
+// steps, with nb x nb Rayleigh-Ritz problems instead of up to 3nb x 3nb ones; LOBPCG with the
+// polynomial as a preconditioner of W (indefinite on the damped interval) stagnated near 1e-2.
+// Bulk work (stencil, Gram, tall GEMMs) runs in FP32 on node-major N x k blocks.
 #include "rw_internal.cuh"
 
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -63,6 +67,15 @@ __global__ void k_colnorms(const float* __restrict__ A, int64_t lda, int64_t N, 
     acc = fmaf(v, v, acc);
   }
   atomicAdd(&out[c], (double)acc);
+}
+
+__global__ void k_scale_cols(float* __restrict__ Y, int64_t ld, int64_t N, int k,
+                             const float* __restrict__ sc) {
+  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= N * k) return;
+  int64_t i = e / k;
+  int j = (int)(e % k);
+  Y[i * ld + j] *= sc[j];
 }
 
 __global__ void k_symmetrize(double* H, int n) {
@@ -118,26 +131,50 @@ struct Work {
   int* cols;
 };
 
+bool trace_on();
+void trace_block(Work& W, const char* what, const float* A, int64_t lda, int k);
+void trace_small(Work& W, const char* what, const double* M, int n);
+
 rw_status gram_into(Work& W, const float* A, int64_t lda, const float* B, int64_t ldb, int p,
                     int q, double* G) {
   return rw_gram(A, lda, B, ldb, W.N, p, q, G, q, false, W.st);
 }
 
-// [Y] (k columns at Y, pitch ld) := orthonormal basis of its span (shifted Cholesky-QR, 2 passes)
+rw_status colnorms(Work& W, const float* A, int64_t lda, int k, std::vector<double>& out);
+
+// [Y] (k columns at Y, pitch ld) := orthonormal basis of its span.  The columns are first
+// scaled to unit norm (the blocks mix residuals of very different sizes); then two passes of
+// shifted Cholesky-QR.  Any shift keeps the span (R is invertible); the first (1e-5 on a unit
+// diagonal, raised 100x and retried if a pivot still fails) is far above the rounding error of
+// a Gram matrix of FP32 columns, and the second pass restores orthonormality to working
+// precision.  Columns must be nonzero.
 rw_status cholqr(Work& W, float* Y, int64_t ld, int k) {
   if (k <= 0) return RW_OK;
+  {
+    std::vector<double> nrm;
+    RW_TRY(colnorms(W, Y, ld, k, nrm));
+    std::vector<float> sc(k);
+    for (int j = 0; j < k; ++j) sc[j] = nrm[j] > 0 ? (float)(1.0 / nrm[j]) : 0.f;
+    RW_CHECK_CUDA(cudaMemcpyAsync(W.lam32 + W.ldS, sc.data(), sizeof(float) * k,
+                                  cudaMemcpyHostToDevice, W.st));
+    k_scale_cols<<<rw_blocks(W.N * k, 256), 256, 0, W.st>>>(Y, ld, W.N, k, W.lam32 + W.ldS);
+    RW_LAUNCH_CHECK();
+  }
   for (int pass = 0; pass < 2; ++pass) {
-    RW_TRY(gram_into(W, Y, ld, Y, ld, k, k, W.G));
-    double tr = 0.0;
-    {
-      std::vector<double> diag(k);
-      RW_CHECK_CUDA(cudaMemcpy2DAsync(diag.data(), sizeof(double), W.G, sizeof(double) * (k + 1),
-                                      sizeof(double), k, cudaMemcpyDeviceToHost, W.st));
+    double shift = pass == 0 ? 1e-5 : 1e-11;
+    for (int attempt = 0;; ++attempt) {
+      RW_TRY(gram_into(W, Y, ld, Y, ld, k, k, W.G));
+      trace_small(W, "cholqr gram", W.G, k);
+      RW_CHECK_CUDA(cudaMemsetAsync(W.flag, 0, sizeof(int), W.st));
+      RW_TRY(rw_cholesky_upper(W.G, k, shift, W.flag, W.st));
+      int bad = 0;
+      RW_CHECK_CUDA(cudaMemcpyAsync(&bad, W.flag, sizeof(int), cudaMemcpyDeviceToHost, W.st));
       RW_CHECK_CUDA(cudaStreamSynchronize(W.st));
-      for (double v : diag) tr += v;
+      if (!bad) break;
+      if (attempt == 3) return RW_ERR_SINGULAR;
+      shift *= 100.0;
     }
-    const double shift = (pass == 0 ? 1e-12 : 1e-15) * (tr > 0 ? tr / k : 1.0);
-    RW_TRY(rw_cholesky_upper(W.G, k, shift, nullptr, W.st));
+    trace_small(W, "cholqr R", W.G, k);
     RW_TRY(rw_tri_inverse_upper(W.G, k, W.Rinv, W.st));
     float* tmp = W.T.as<float>();
     RW_TRY(rw_gemm_tall(Y, ld, W.Rinv, k, W.N, k, k, 1.f, 0.f, tmp, W.ldS, W.st));
@@ -190,6 +227,44 @@ rw_status cheb_filter(Work& W, float* Y, int64_t ld, int k, int deg, double a0, 
   return RW_OK;
 }
 
+rw_status colnorms(Work& W, const float* A, int64_t lda, int k, std::vector<double>& out);
+
+// opt-in diagnostics (environment variable RW_TRACE_EIG): per-step column-norm ranges
+bool trace_on() {
+  static int on = -1;
+  if (on < 0) on = getenv("RW_TRACE_EIG") ? 1 : 0;
+  return on == 1;
+}
+
+void trace_block(Work& W, const char* what, const float* A, int64_t lda, int k) {
+  if (!trace_on() || k <= 0) return;
+  std::vector<double> v;
+  if (colnorms(W, A, lda, k, v) != RW_OK) return;
+  double lo = 1e300, hi = 0.0;
+  int bad = -1;
+  for (int j = 0; j < k; ++j) {
+    if (!std::isfinite(v[j]) && bad < 0) bad = j;
+    lo = std::min(lo, v[j]);
+    hi = std::max(hi, v[j]);
+  }
+  fprintf(stderr, "[rw eig] %-14s k=%4d norms [%.3e, %.3e] first-nonfinite=%d\n", what, k, lo, hi,
+          bad);
+}
+
+void trace_small(Work& W, const char* what, const double* M, int n) {
+  if (!trace_on()) return;
+  std::vector<double> h((size_t)n * n);
+  cudaMemcpyAsync(h.data(), M, sizeof(double) * n * n, cudaMemcpyDeviceToHost, W.st);
+  cudaStreamSynchronize(W.st);
+  double mx = 0.0;
+  int bad = -1;
+  for (size_t e = 0; e < h.size(); ++e) {
+    if (!std::isfinite(h[e]) && bad < 0) bad = (int)e;
+    mx = std::max(mx, std::fabs(h[e]));
+  }
+  fprintf(stderr, "[rw eig] %-14s n=%4d max|.|=%.3e first-nonfinite=%d\n", what, n, mx, bad);
+}
+
 rw_status colnorms(Work& W, const float* A, int64_t lda, int k, std::vector<double>& out) {
   RW_CHECK_CUDA(cudaMemsetAsync(W.cn, 0, sizeof(double) * k, W.st));
   const int sms = g_rw_num_sms > 0 ? g_rw_num_sms : 148;
@@ -211,7 +286,9 @@ rw_status rayleigh_ritz(Work& W, const float* S, const float* AS, int n, int k,
   RW_TRY(rw_gram(S, W.ldS, AS, W.ldS, W.N, n, n, W.H, n, false, W.st));
   k_symmetrize<<<rw_blocks((int64_t)n * n, 256), 256, 0, W.st>>>(W.H, n);
   RW_LAUNCH_CHECK();
+  trace_small(W, "rr H", W.H, n);
   RW_TRY(rw_sym_eig(W.H, n, W.w, W.V, W.eigw, W.st));
+  trace_small(W, "rr V", W.V, n);
   w_h.resize(n);
   RW_CHECK_CUDA(cudaMemcpyAsync(w_h.data(), W.w, sizeof(double) * n, cudaMemcpyDeviceToHost, W.st));
   RW_CHECK_CUDA(cudaStreamSynchronize(W.st));
@@ -331,7 +408,7 @@ extern "C" rw_status rw_precompute(rw_graph* g, const rw_eig_opts* opts, void* s
          ow = take(sizeof(double) * nmax), oE = take(rw_sym_eig_work_bytes(nmax)),
          oG = take(sizeof(double) * nmax * nmax), ocn = take(sizeof(double) * nmax),
          oC = take(sizeof(float) * nmax * nmax), oR = take(sizeof(float) * nmax * nmax),
-         oL = take(sizeof(float) * nmax), of = take(sizeof(int) * 16),
+         oL = take(sizeof(float) * (2 * (size_t)W.ldS + nmax)), of = take(sizeof(int) * 16),
          oc = take(sizeof(int) * nmax);
   RW_TRY(W.small.grow(off));
   char* sb = W.small.as<char>();
@@ -380,7 +457,8 @@ extern "C" rw_status rw_precompute(rw_graph* g, const rw_eig_opts* opts, void* s
   }
   int n_p = 0;
   int it = 0;
-  const double switch_res = 1e-3;  // filtered-subspace steps while the worst residual is above
+  int stalls = 0;                   // consecutive filtered steps that cut the residual < 30%
+  double prev_maxres = 1e300;
   float* T = W.T.as<float>();
   int conv = 0;
   double maxres = 0.0;
@@ -401,10 +479,17 @@ extern "C" rw_status rw_precompute(rw_graph* g, const rw_eig_opts* opts, void* s
     maxres = 0.0;
     for (int j = 0; j < m; ++j) maxres = std::max(maxres, res[j]);
     if (conv >= m) break;
-    if (deg > 0 && maxres > switch_res) {
+    if (trace_on())
+      fprintf(stderr, "[rw eig] it=%d conv=%d maxres=%.3e lam0=%.6e lam_nb=%.6e\n", it, conv, maxres,
+              lam[0], lam[nb - 1]);
+    if (deg > 0 && stalls < 2) {
+      stalls = (maxres > 0.7 * prev_maxres) ? stalls + 1 : 0;
+      prev_maxres = maxres;
       // filtered subspace step: X <- orth(p(Op) X), Rayleigh-Ritz on nb columns
       RW_TRY(cheb_filter(W, S, ld, nb, deg, std::min(lam[0], 0.0), lam[nb - 1], upper, &applies));
+      trace_block(W, "filtered X", S, ld, nb);
       RW_TRY(cholqr(W, S, ld, nb));
+      trace_block(W, "orth X", S, ld, nb);
       RW_TRY(rw_stencil_apply(g, S, ld, AS, ld, nb, 1.f, 0.f, nullptr, 0, 0.f, W.st));
       ++applies;
       RW_TRY(rayleigh_ritz(W, S, AS, nb, nb, wh));
@@ -433,10 +518,33 @@ extern "C" rw_status rw_precompute(rw_graph* g, const rw_eig_opts* opts, void* s
       RW_CHECK_CUDA(cudaMemcpyAsync(W.cols, pc.data(), sizeof(int) * np_use, cudaMemcpyHostToDevice, W.st));
       RW_TRY(rw_copy_cols(W.Pb.as<float>(), ld, S + nb + n_act, ld, g->N, W.cols, np_use, W.st));
     }
-    const int nw = n_act + np_use;
+    int nw = n_act + np_use;
+    {
+      // drop columns that vanished (e.g. the previous direction of a column that stopped
+      // moving); Cholesky-QR needs nonzero columns
+      std::vector<double> nrm;
+      RW_TRY(colnorms(W, S + nb, ld, nw, nrm));
+      double mx = 0.0;
+      for (double v : nrm) mx = std::max(mx, v);
+      std::vector<int> keep;
+      for (int j = 0; j < nw; ++j)
+        if (nrm[j] > 1e-30 && nrm[j] > 1e-12 * mx) keep.push_back(j);
+      if ((int)keep.size() < nw) {
+        RW_CHECK_CUDA(cudaMemcpyAsync(W.cols, keep.data(), sizeof(int) * keep.size(),
+                                      cudaMemcpyHostToDevice, W.st));
+        RW_TRY(rw_copy_cols(S + nb, ld, T, ld, g->N, W.cols, (int)keep.size(), W.st));
+        RW_CHECK_CUDA(cudaMemcpy2DAsync(S + nb, sizeof(float) * ld, T, sizeof(float) * ld,
+                                        sizeof(float) * keep.size(), g->N,
+                                        cudaMemcpyDeviceToDevice, W.st));
+        nw = (int)keep.size();
+      }
+    }
     const int ntot = nb + nw;
+    trace_block(W, "W P raw", S + nb, ld, nw);
     RW_TRY(orth_against(W, S, ld, nb, S + nb, ld, nw));
+    trace_block(W, "W P orth", S + nb, ld, nw);
     RW_TRY(cholqr(W, S + nb, ld, nw));
+    trace_block(W, "W P cholqr", S + nb, ld, nw);
     RW_TRY(rw_stencil_apply(g, S + nb, ld, AS + nb, ld, nw, 1.f, 0.f, nullptr, 0, 0.f, W.st));
     ++applies;
     RW_TRY(rayleigh_ritz(W, S, AS, ntot, nb, wh));
