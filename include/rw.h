@@ -282,6 +282,25 @@ rw_status rw_grad_exact(const rw_graph* g, const int32_t* seed_idx_dev,
                         const float* dloss_dU_dev, double rel_tol, int32_t max_iter,
                         float* grad_w_dev, double* grad_beta_host, void* stream);
 
+/* ------------------------------------------------------------------------------------------
+ * Rayleigh quotients of caller columns with no device allocation.  The paper has no
+ * counterpart; this serves callers that cannot allocate device memory during a call (a host
+ * application that owns the whole device memory budget through its own pool, or a thread that
+ * must not enter the allocator).  It returns the same values as the value update of
+ * Sec. III-B with unchanged weights: lambda_dev[i] = sum_e w_e (q_i(a) s_a - q_i(b) s_b)^2 /
+ * ||q_i||^2 for the m columns of Q_dev (N x m node-major, pitch ldq a multiple of 4, >= m,
+ * 16-byte aligned) under g's current weights; lambda_dev holds m doubles on the device.
+ * Scratch: a fixed device array inside the library (about 2 MiB, held by every GPU that loads
+ * the library until exit), no cudaMalloc or cudaFree.  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress); make that first call before any stream
+ * capture.  All calls share the array: calls that overlap on the GPU race.  m > 1024 (or any
+ * other bad argument) returns RW_ERR_INVALID_ARG with a message in rw_last_error_message().
+ * Asynchronous on `stream`.
+ * ---------------------------------------------------------------------------------------- */
+#define RW_NOALLOC_MAX_M 1024
+rw_status rw_rayleigh_quotients_noalloc(const rw_graph* g, const float* Q_dev, int64_t ldq,
+                                        int32_t m, double* lambda_dev, void* stream);
+
 /* Writes the Gaussian-fit priors of Sec. IV-A (N x n_labels, node-major) for the seeds. */
 rw_status rw_solve_priors(const rw_graph* g, const int32_t* seed_idx_dev,
                           const int32_t* seed_lab_dev, int32_t S, int32_t n_labels,

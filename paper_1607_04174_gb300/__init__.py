@@ -233,3 +233,10 @@ def rw_solve_priors(g, seed_idx, seed_lab, n_labels, priors, stream=None):
     return _check(abi.lib().rw_solve_priors(g, _p(seed_idx), _p(seed_lab), len(seed_idx),
                                             n_labels, _p(priors), _stream(stream)),
                   "rw_solve_priors")
+
+
+def rw_rayleigh_quotients_noalloc(g, Q, lam_out, m=None, stream=None):
+    m = Q.shape[1] if m is None else m
+    return _check(abi.lib().rw_rayleigh_quotients_noalloc(g, _p(Q), _ld(Q), m, _p(lam_out),
+                                                          _stream(stream)),
+                  "rw_rayleigh_quotients_noalloc")

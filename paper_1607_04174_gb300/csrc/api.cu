@@ -19,6 +19,8 @@ void rw_set_last_cuda_error(cudaError_t e, const char* what, const char* file, i
            line);
 }
 
+void rw_set_error_message(const char* msg) { snprintf(g_last_err, sizeof(g_last_err), "%s", msg); }
+
 extern "C" const char* rw_last_error_message(void) { return g_last_err; }
 
 rw_status rw_device_init() {

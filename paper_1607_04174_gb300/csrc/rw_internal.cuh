@@ -32,6 +32,7 @@ void rw_count_launch();
   } while (0)
 
 void rw_set_last_cuda_error(cudaError_t e, const char* what, const char* file, int line);
+void rw_set_error_message(const char* msg);
 
 // Device status word bits (ORed by kernels, read by the host).
 enum : int {

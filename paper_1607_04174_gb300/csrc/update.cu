@@ -540,3 +540,85 @@ extern "C" rw_status rw_update_topology(rw_graph* g, rw_basis* b, const rw_topol
   }
   return RW_ERR_INVALID_ARG;
 }
+
+// ---------------------------------------------------------------------------------------
+// Rayleigh quotients without any allocation.
+//
+// Some callers cannot allocate device memory during a call: for example a host application
+// that owns the whole device memory budget through its own pool and forbids libraries from
+// calling cudaMalloc, or a latency-critical thread that must not hit the allocator.  This
+// entry point computes the same edge-sum Rayleigh quotients as the value update, but keeps
+// its scratch (per-block partial sums and column norms) in the file-scope device array below
+// instead of the graph's scratch buffers.  Every GPU that loads the library holds the array
+// (about 2 MiB) until the process exits.  All calls share it and it keeps the last call's
+// contents, so the norm accumulators are cleared at the start of every call and calls that
+// overlap on the GPU (different streams, or different host threads) race on it.
+// ---------------------------------------------------------------------------------------
+namespace {
+constexpr int kNoAllocBlocks = 256;            // blocks of the partial-sum kernel
+constexpr int kNoAllocWidth = 32 * 4 * 8;      // columns of one partial row (m <= 1024)
+constexpr size_t kNoAllocDoubles = (size_t)kNoAllocBlocks * kNoAllocWidth + kNoAllocWidth;
+}  // namespace
+
+static __device__ __align__(256) double g_noalloc_scratch[kNoAllocDoubles];
+
+#include <mutex>
+
+static std::mutex g_noalloc_mu;
+static double* g_noalloc_ptr[128] = {};  // host-usable address of the array, per device
+
+extern "C" rw_status rw_rayleigh_quotients_noalloc(const rw_graph* g, const float* Q_dev,
+                                                   int64_t ldq, int32_t m, double* lambda_dev,
+                                                   void* stream) {
+  if (!g || !Q_dev || !lambda_dev) return RW_ERR_INVALID_ARG;
+  if (m < 1 || m > RW_NOALLOC_MAX_M) {
+    rw_set_error_message("rw_rayleigh_quotients_noalloc: m must be in [1, 1024]");
+    return RW_ERR_INVALID_ARG;
+  }
+  if (ldq < m || (ldq & 3) || (reinterpret_cast<uintptr_t>(Q_dev) & 15)) {
+    rw_set_error_message("rw_rayleigh_quotients_noalloc: ldq must be >= m and a multiple of 4, "
+                         "Q_dev 16-byte aligned");
+    return RW_ERR_INVALID_ARG;
+  }
+  int dev = 0;
+  RW_CHECK_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 128) return RW_ERR_UNSUPPORTED;
+  double* scratch = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+      // first call on this device: the host-side name of the array is not a device address
+      void* p = nullptr;
+      RW_CHECK_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+      g_noalloc_ptr[dev] = static_cast<double*>(p);
+    }
+    scratch = g_noalloc_ptr[dev];
+  }
+  if (g_rw_num_sms <= 0) RW_TRY(rw_device_init());
+  cudaStream_t st = rw_stream(stream);
+  double* part = scratch;
+  double* qn = scratch + (size_t)kNoAllocBlocks * kNoAllocWidth;
+  RW_CHECK_CUDA(cudaMemsetAsync(qn, 0, sizeof(double) * m, st));
+  int64_t rpb = 4096;
+  dim3 grid((unsigned)((g->N + rpb - 1) / rpb), (unsigned)((m + 255) / 256));
+  k_qnorm2<<<grid, 256, 0, st>>>(Q_dev, ldq, g->N, m, rpb, qn);
+  RW_LAUNCH_CHECK();
+  const int nch = (m + 3) / 4;
+  const int ch = (nch + 31) / 32;
+  Box fb = full_box(g);
+  switch (ch) {
+    case 1: launch_rayleigh<1>(g, Q_dev, ldq, nch, fb, 0, fb, nullptr, kNoAllocBlocks, part, st); break;
+    case 2: launch_rayleigh<2>(g, Q_dev, ldq, nch, fb, 0, fb, nullptr, kNoAllocBlocks, part, st); break;
+    case 3: launch_rayleigh<3>(g, Q_dev, ldq, nch, fb, 0, fb, nullptr, kNoAllocBlocks, part, st); break;
+    case 4: launch_rayleigh<4>(g, Q_dev, ldq, nch, fb, 0, fb, nullptr, kNoAllocBlocks, part, st); break;
+    case 5: launch_rayleigh<5>(g, Q_dev, ldq, nch, fb, 0, fb, nullptr, kNoAllocBlocks, part, st); break;
+    case 6: launch_rayleigh<6>(g, Q_dev, ldq, nch, fb, 0, fb, nullptr, kNoAllocBlocks, part, st); break;
+    case 7: launch_rayleigh<7>(g, Q_dev, ldq, nch, fb, 0, fb, nullptr, kNoAllocBlocks, part, st); break;
+    default: launch_rayleigh<8>(g, Q_dev, ldq, nch, fb, 0, fb, nullptr, kNoAllocBlocks, part, st); break;
+  }
+  RW_LAUNCH_CHECK();
+  k_rayleigh_finish<<<rw_blocks(m, 128), 128, 0, st>>>(part, kNoAllocBlocks, 32 * 4 * ch, m, qn,
+                                                      1.0, lambda_dev, 0);
+  RW_LAUNCH_CHECK();
+  return RW_OK;
+}
