@@ -107,7 +107,7 @@ __global__ void k_to_basis(const float* __restrict__ X, int64_t ldx, int64_t N, 
   int c = (int)(e % ld16);
   float v = (c < m) ? X[i * ldx + c] : 0.f;
   if (c < ld32) Q32[i * ld32 + c] = v;
-  Q16[e] = __float2half_rn(v * qscale);
+  Q16[((int64_t)(c / 8) * N + i) * 8 + (c % 8)] = __float2half_rn(v * qscale);  // panel-major
 }
 
 __global__ void k_maxf(const float* __restrict__ v, int64_t n, unsigned int* out) {

@@ -111,8 +111,9 @@ struct rw_basis {
   int ld32 = 0;           // row pitch of Q32 (multiple of 4)
   int ld16 = 0;           // row pitch of the 16-bit copies (multiple of 8)
   float* Q32 = nullptr;   // N x ld32
-  __half* Q16 = nullptr;  // N x ld16, scaled by qscale (power of two)
-  __nv_bfloat16* Qbf = nullptr;  // N x ld16, unscaled, built on first use
+  __half* Q16 = nullptr;  // N x ld16, scaled by qscale (power of two), panel-major: column
+                          // 8c + v of row i at ((c N + i) 8 + v)
+  __nv_bfloat16* Qbf = nullptr;  // same layout, unscaled, built on first use
   float qscale = 1.f;
   double* lam = nullptr;  // m values on the device
   double* lam_host = nullptr;

@@ -30,34 +30,27 @@ constexpr int kMaxSmallM = 224;  // m x m FP32 factorizations live in one CTA's 
 int lpad_of(int L) { return L <= 4 ? 4 : (L <= 8 ? 8 : 16); }
 
 struct Layout {
-  size_t stats, fit, cnt, mdev, Qs, Xs, Us, R0, G, K, bv, h, cu, Z, C, fc, pass, cand, lam,
-      fit64, part, total;
+  size_t mdev, Bcat, Gcat, Z, C, fu, nrm, cand, Lg, zg, scal, part, total;
 };
 
-Layout make_layout(int S, int mp, int mq, int lp, int ncand, int nblk_part) {
+// wcat = 2 mp + 2 lp: the seed-side block [X | Q_s | r0 | U-hat_s] (S x wcat, one row per
+// seed) and its product with Q_s, [K | G | h | b] = Q_s^T [X | Q_s | r0 | U-hat_s] (mp x wcat)
+Layout make_layout(int S, int mp, int mq, int lp, int L, int ncand, int nblk_part) {
   Layout o;
   size_t off = 0;
   auto take = [&](size_t bytes) { size_t r = off; off += (bytes + 255) & ~size_t(255); return r; };
-  o.stats = take(sizeof(double) * 16 * 3);
-  o.fit = take(sizeof(float) * 16 * 3);
-  o.cnt = take(sizeof(int) * 16);
+  const size_t wcat = 2 * (size_t)mp + 2 * (size_t)lp;
   o.mdev = take(sizeof(int) * 8);
-  o.Qs = take(sizeof(float) * (size_t)S * mp);
-  o.Xs = take(sizeof(float) * (size_t)S * mp);
-  o.Us = take(sizeof(float) * (size_t)S * lp);
-  o.R0 = take(sizeof(float) * (size_t)S * lp);
-  o.G = take(sizeof(double) * (size_t)mp * mp);
-  o.K = take(sizeof(double) * (size_t)mp * mp);
-  o.bv = take(sizeof(double) * (size_t)mp * lp);
-  o.h = take(sizeof(double) * (size_t)mp * lp);
-  o.cu = take(sizeof(double) * (size_t)lp * lp);
+  o.Bcat = take(sizeof(float) * (size_t)S * wcat);
+  o.Gcat = take(sizeof(double) * (size_t)mp * wcat);
   o.Z = take(sizeof(double) * (size_t)mq * lp);
   o.C = take(sizeof(float) * (size_t)mq * lp);
-  o.fc = take(sizeof(double) * (size_t)(ncand + 1) * lp);
-  o.pass = take(sizeof(int) * (size_t)(ncand + 1));
+  o.fu = take(sizeof(double) * (size_t)(ncand + 1) * RW_MAX_LABELS + sizeof(double) * lp);
+  o.nrm = take(sizeof(float) * (size_t)(ncand + 1) * RW_MAX_LABELS);
   o.cand = take(sizeof(int) * (size_t)(ncand + 1));
-  o.lam = take(sizeof(float) * (size_t)mp);
-  o.fit64 = take(sizeof(double) * 16 * 2);
+  o.Lg = take(sizeof(float) * (size_t)mp * mp);
+  o.zg = take(sizeof(float) * (size_t)L * mp);
+  o.scal = take(sizeof(float) * 8);
   o.part = take(sizeof(float) * (size_t)nblk_part * mq * lp);
   o.total = off;
   return o;
@@ -156,17 +149,18 @@ __global__ void k_seed_gather(const int32_t* __restrict__ idx, const int32_t* __
                               const float* __restrict__ sq, int normalized, int kind, int ndim,
                               int DX, int DY, int DZ, const int32_t* __restrict__ rowptr,
                               const int32_t* __restrict__ colv, const float* __restrict__ ccsr,
-                              float gamma, float* __restrict__ Qs, float* __restrict__ Xs,
-                              float* __restrict__ Us, float* __restrict__ R0) {
+                              float gamma, float* __restrict__ Bcat, int ldb) {
   const int lane = threadIdx.x & 31;
   const int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (t >= S) return;
   const int i = idx[t], k0 = lab[t];
-  float* qs = Qs + (int64_t)t * mp;
-  float* xs = Xs + (int64_t)t * mp;
+  float* xs = Bcat + (int64_t)t * ldb;
+  float* qs = xs + mp;
+  float* R0 = qs + mp;
+  float* Us = R0 + lp;
   if (i < 0 || (int64_t)i >= N || k0 < 0 || k0 >= L) {  // reported by k_seed_scatter
     for (int c = lane; c < mp; c += 32) { qs[c] = 0.f; xs[c] = 0.f; }
-    if (lane < lp) { Us[t * lp + lane] = 0.f; R0[t * lp + lane] = 0.f; }
+    if (lane < lp) { Us[lane] = 0.f; R0[lane] = 0.f; }
     return;
   }
   const float* qi = Q + (int64_t)i * ldq;
@@ -196,183 +190,492 @@ __global__ void k_seed_gather(const int32_t* __restrict__ idx, const int32_t* __
   }
   if (lane < lp) {
     float u = (lane == k0) ? sq[i] : 0.f;
-    Us[t * lp + lane] = u;
-    R0[t * lp + lane] = (lane < L) ? r0 + gamma * u : 0.f;
+    Us[lane] = u;
+    R0[lane] = (lane < L) ? r0 + gamma * u : 0.f;
   }
 }
 
 // ---------------------------------------------------------------------------------------
-// Shared-memory FP32 helpers for one CTA (row stride ms, odd to avoid bank conflicts)
+// Shared-memory FP32 dense kernels for one CTA (row stride ms, odd, so column walks are free
+// of bank conflicts).
 // ---------------------------------------------------------------------------------------
-__device__ bool chol_lower_smem(float* A, int m, int ms) {
-  __shared__ int bad;
-  if (threadIdx.x == 0) bad = 0;
-  for (int k = 0; k < m; ++k) {
-    __syncthreads();
-    float piv = A[k * ms + k];
-    if (!(piv > 0.f)) {
-      if (threadIdx.x == 0) bad = 1;
-      piv = 1e-30f;
+// Cholesky of the kb x kb diagonal block at (k0, k0) by one warp in shared memory: lane r owns
+// row r; step kk uses the unscaled column (l_rc = a_r,kk a_c,kk / a_kk,kk), then the column is
+// scaled in one pass.  A compact loop (no unrolling: this runs once per tile on one warp).
+// dinv[0..kb) receives 1 / L_ii.
+__device__ void chol_diag_block_warp(float* A, int ms, int k0, int kb, float* dinv, int* bad) {
+  const int lane = threadIdx.x & 31;
+  float* T = A + k0 * ms + k0;
+  for (int kk = 0; kk < kb; ++kk) {
+    float piv = T[kk * ms + kk];
+    if (!(piv > 0.f)) piv = 1e-30f;
+    const float inv = 1.f / piv;
+    if (lane > kk && lane < kb) {
+      const float a = T[lane * ms + kk] * inv;
+      for (int c = kk + 1; c <= lane; ++c) T[lane * ms + c] = fmaf(-a, T[c * ms + kk], T[lane * ms + c]);
     }
-    const float r = sqrtf(piv);
-    __syncthreads();
-    for (int i = k + 1 + threadIdx.x; i < m; i += blockDim.x) A[i * ms + k] /= r;
-    if (threadIdx.x == 0) A[k * ms + k] = r;
-    __syncthreads();
-    const int w = m - k - 1;
-    for (int e = threadIdx.x; e < w * w; e += blockDim.x) {
-      int i = k + 1 + e / w, j = k + 1 + e % w;
-      if (j <= i) A[i * ms + j] = fmaf(-A[i * ms + k], A[j * ms + k], A[i * ms + j]);
+    __syncwarp();
+  }
+  float di = 1.f;
+  if (lane < kb) {
+    float piv = T[lane * ms + lane];
+    if (!(piv > 0.f)) { *bad = 1; piv = 1e-30f; }
+    di = rsqrtf(piv);
+    dinv[lane] = di;
+  }
+  __syncwarp();
+  if (lane < kb) {
+    for (int c = 0; c < lane; ++c) T[lane * ms + c] *= dinv[c];
+    T[lane * ms + lane] = 1.f / di;
+  }
+  __syncwarp();
+}
+
+// Cholesky of the kb x kb diagonal block at (k0, k0) by the whole CTA in shared memory.  Step
+// kk uses the unscaled column (l_r l_c = a_r,kk a_c,kk / a_kk,kk), so one barrier per step
+// suffices; the column scaling and the square roots follow in one pass.  dinv[0..kb) receives
+// the reciprocals of the diagonal of L.
+__device__ void chol_diag_block_cta(float* A, int ms, int k0, int kb, float* dinv, int* bad) {
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5, nty = blockDim.x >> 5;
+  float* T = A + k0 * ms + k0;
+  for (int kk = 0; kk < kb; ++kk) {
+    float piv = T[kk * ms + kk];
+    if (!(piv > 0.f)) piv = 1e-30f;
+    const float inv = 1.f / piv;
+    for (int r = kk + 1 + ty; r < kb; r += nty) {
+      const int c = kk + 1 + tx;
+      if (c <= r) T[r * ms + c] = fmaf(-T[r * ms + kk] * inv, T[c * ms + kk], T[r * ms + c]);
     }
+    __syncthreads();
+  }
+  if (threadIdx.x < kb) {
+    float piv = T[threadIdx.x * ms + threadIdx.x];
+    if (!(piv > 0.f)) { *bad = 1; piv = 1e-30f; }
+    const float d = sqrtf(piv);
+    dinv[threadIdx.x] = 1.f / d;
   }
   __syncthreads();
+  for (int r = ty; r < kb; r += nty) {
+    const int c = tx;
+    if (c < r) T[r * ms + c] *= dinv[c];
+    else if (c == r) T[r * ms + c] = 1.f / dinv[c];
+  }
+  __syncthreads();
+}
+
+// Blocked right-looking Cholesky A = L L^T (lower, in place), 32-column panels.
+__device__ bool chol_lower_smem(float* A, int m, int ms) {
+  __shared__ int bad;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  if (tid == 0) bad = 0;
+  __syncthreads();
+  for (int k0 = 0; k0 < m; k0 += 32) {
+    const int kb = min(32, m - k0);
+    __shared__ float dloc[32];
+    chol_diag_block_cta(A, ms, k0, kb, dloc, &bad);
+    // L21 = A21 L11^{-T}: one thread per row below the panel
+    for (int r = k0 + kb + tid; r < m; r += blockDim.x) {
+      float* ar = A + r * ms + k0;
+      for (int j = 0; j < kb; ++j) {
+        const float* lj = A + (k0 + j) * ms + k0;
+        float s = ar[j];
+        for (int t = 0; t < j; ++t) s = fmaf(-ar[t], lj[t], s);
+        ar[j] = s / lj[j];
+      }
+    }
+    __syncthreads();
+    // A22 -= L21 L21^T (lower): a warp per row, lanes over columns
+    const int r0 = k0 + kb;
+    for (int i = r0 + warp; i < m; i += nw) {
+      const float* li = A + i * ms + k0;
+      for (int j = r0 + lane; j <= i; j += 32) {
+        const float* lj = A + j * ms + k0;
+        float s = 0.f;
+        for (int t = 0; t < kb; ++t) s = fmaf(li[t], lj[t], s);
+        A[i * ms + j] -= s;
+      }
+    }
+    __syncthreads();
+  }
   return bad == 0;
 }
 
-// one warp: L z = b (forward), L lower with stride ms
+// one warp: L z = b (forward, column-oriented: after z_i is known, every later entry is
+// updated in parallel).  b and z may alias.
 __device__ void fwd_lower_warp(const float* A, int m, int ms, const float* b, float* z) {
   const int lane = threadIdx.x & 31;
+  for (int i = lane; i < m; i += 32) z[i] = b[i];
+  __syncwarp();
   for (int i = 0; i < m; ++i) {
-    float s = 0.f;
-    for (int j = lane; j < i; j += 32) s = fmaf(A[i * ms + j], z[j], s);
-    s = warp_sum(s);
-    if (lane == 0) z[i] = (b[i] - s) / A[i * ms + i];
+    const float zi = z[i] / A[i * ms + i];
+    __syncwarp();
+    if (lane == 0) z[i] = zi;
+    for (int j = i + 1 + lane; j < m; j += 32) z[j] = fmaf(-A[j * ms + i], zi, z[j]);
     __syncwarp();
   }
 }
 
-// one warp: L^T x = z (backward)
+// one warp: L^T x = z with the reciprocals of diag(L) given; lane t keeps x[t + 32 q] in
+// registers (m <= 224), the newly final x_i is broadcast by shuffle
+__device__ void bwd_lowerT_warp_reg(const float* __restrict__ A, int m, int ms,
+                                    const float* __restrict__ dinv, const float* z, float* x) {
+  const int lane = threadIdx.x & 31;
+  float xr[7];
+#pragma unroll
+  for (int q = 0; q < 7; ++q) xr[q] = (lane + 32 * q < m) ? z[lane + 32 * q] : 0.f;
+  for (int i = m - 1; i >= 0; --i) {
+    const int qi = i >> 5, li = i & 31;
+    float own = 0.f;
+#pragma unroll
+    for (int q = 0; q < 7; ++q) own = (q == qi) ? xr[q] : own;
+    const float xi = __shfl_sync(0xffffffff, own, li) * dinv[i];
+    const float* ai = A + i * ms;
+#pragma unroll
+    for (int q = 0; q < 7; ++q) {
+      const int j = lane + 32 * q;
+      if (j < i) xr[q] = fmaf(-ai[j], xi, xr[q]);
+      else if (j == i) xr[q] = xi;
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < 7; ++q)
+    if (lane + 32 * q < m) x[lane + 32 * q] = xr[q];
+  __syncwarp();
+}
+
+// one warp: L^T x = z (backward, column-oriented).  z and x may alias.
 __device__ void bwd_lowerT_warp(const float* A, int m, int ms, const float* z, float* x) {
   const int lane = threadIdx.x & 31;
+  for (int i = lane; i < m; i += 32) x[i] = z[i];
+  __syncwarp();
   for (int i = m - 1; i >= 0; --i) {
-    float s = 0.f;
-    for (int j = i + 1 + lane; j < m; j += 32) s = fmaf(A[j * ms + i], x[j], s);
-    s = warp_sum(s);
-    if (lane == 0) x[i] = (z[i] - s) / A[i * ms + i];
+    const float xi = x[i] / A[i * ms + i];
+    __syncwarp();
+    if (lane == 0) x[i] = xi;
+    for (int j = lane; j < i; j += 32) x[j] = fmaf(-A[i * ms + j], xi, x[j]);
     __syncwarp();
   }
 }
 
-// ---------------------------------------------------------------------------------------
-// Adaptive m (Sec. III-A-1, Eq. alpha_1).  One CTA per candidate m: f_k(m) =
-// min_{||a|| <= rho} ||Q_s^{(m)} a - u-hat_s^k||^2.  G_m + mu0 I = L L^T (FP32, mu0 a tiny
-// relative shift); a = (G_m + mu I)^{-1} b_k with mu = mu0 if ||a|| <= rho, else mu from Newton
-// on 1/||a(mu)|| - 1/rho (More-Sorensen); f evaluated directly as the squared residual over
-// the S seeds.
-// ---------------------------------------------------------------------------------------
 __device__ void load_shifted_gram(float* A, int m, int ms, const double* G, int ldg, float mu) {
-  for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
-    int i = e / m, j = e % m;
-    A[i * ms + j] = (float)G[(int64_t)i * ldg + j] + (i == j ? mu : 0.f);
-  }
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5, nty = blockDim.x >> 5;
+  for (int i = ty; i < m; i += nty)
+    for (int j = tx; j <= i; j += 32)
+      A[i * ms + j] = (float)G[(int64_t)i * ldg + j] + (i == j ? mu : 0.f);
 }
 
-__global__ void __launch_bounds__(1024)
-k_adapt(const double* __restrict__ G, int ldg, const double* __restrict__ bv, int lp,
-        const float* __restrict__ Qs, int mp, const float* __restrict__ Us, int S, int L,
-        const int* __restrict__ cand, double rho, double fmax, double* __restrict__ fout,
-        int* __restrict__ pass) {
-  extern __shared__ float sm[];
-  const int m = cand[blockIdx.x];
-  const int ms = m | 1;
-  float* A = sm;                       // m x ms
-  float* al = A + (size_t)m * ms;      // L x m   solutions
-  float* z = al + (size_t)L * m;       // L x m   temporaries
-  float* bb = z + (size_t)L * m;       // L x m   right-hand sides
-  __shared__ float mu0s, red[32];
-  __shared__ float fk[RW_MAX_LABELS], nrm[RW_MAX_LABELS];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  for (int e = threadIdx.x; e < L * m; e += blockDim.x) {
-    int k = e / m, i = e % m;
-    bb[k * m + i] = (float)bv[(int64_t)i * lp + k];
+// f_k = || Q_s^{(m)} alpha_k - u_k ||^2 over the seeds: a warp per seed row (lanes over the
+// columns), all labels at once; result in fk[0..L)
+__device__ void seed_residuals(const float* __restrict__ Qs, int ldq, const float* __restrict__ Us,
+                               int ldu, int S, int L, int m, const float* al, float* fk, int alm) {
+  // f_k = || Q_s^{(m)} alpha_k - u_k ||^2 over the seeds.  A warp takes 4 seeds at a time
+  // (lanes over the columns), labels in groups of 4; the 16 (seed, label) dot products are
+  // reduced across the warp by a reduce-scatter butterfly (even lane 2j holds sum j).
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if (threadIdx.x < RW_MAX_LABELS) fk[threadIdx.x] = 0.f;
+  __syncthreads();
+  for (int k0 = 0; k0 < L; k0 += 4) {
+    float acc = 0.f;  // lane 2j accumulates the squared residuals of entry j = 4 q + t
+    for (int s0 = 4 * warp; s0 < S; s0 += 4 * nw) {
+      float val[16];
+#pragma unroll
+      for (int e = 0; e < 16; ++e) val[e] = 0.f;
+      for (int j = lane; j < m; j += 32) {
+        float a[4];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) a[t] = (k0 + t < L) ? al[(k0 + t) * alm + j] : 0.f;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const float qj = (s0 + q < S) ? Qs[(int64_t)(s0 + q) * ldq + j] : 0.f;
+#pragma unroll
+          for (int t = 0; t < 4; ++t) val[4 * q + t] = fmaf(qj, a[t], val[4 * q + t]);
+        }
+      }
+#pragma unroll
+      for (int half = 8, off = 16; half >= 1; half >>= 1, off >>= 1) {
+        const bool up = (lane & off) != 0;
+#pragma unroll
+        for (int t = 0; t < half; ++t) {
+          const float send = up ? val[t] : val[t + half];
+          const float keep = up ? val[t + half] : val[t];
+          val[t] = keep + __shfl_xor_sync(0xffffffff, send, off);
+        }
+      }
+      const float sum = val[0] + __shfl_xor_sync(0xffffffff, val[0], 1);
+      const int jj = lane >> 1, q = jj >> 2, t = jj & 3;
+      if ((lane & 1) == 0 && s0 + q < S && k0 + t < L) {
+        const float r = sum - Us[(int64_t)(s0 + q) * ldu + k0 + t];
+        acc = fmaf(r, r, acc);
+      }
+    }
+    // lanes 2j with j % 4 == t hold label k0 + t
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      float v = ((lane & 1) == 0 && ((lane >> 1) & 3) == t) ? acc : 0.f;
+      v = warp_sum(v);
+      if (lane == 0 && k0 + t < L) atomicAdd(&fk[k0 + t], v);
+    }
   }
-  if (threadIdx.x == 0) {
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------------------------------
+// Adaptive m (Sec. III-A-1, Eq. alpha_1) in one CTA of 256 threads:
+//   f_k(m) = min_{||a|| <= rho} || Q_s^{(m)} a - u_k ||^2,  candidates m = m_step, 2 m_step, ...
+// The candidates are nested, so the Cholesky factor of G + mu0 I (G = Q_s^T Q_s, mu0 = 1e-6
+// tr G / m_max) and z_k = L^{-1} b_k (b = Q_s^T U-hat_s) are grown 32 rows at a time
+// (left-looking, "add eigenvectors and repeat") and stop at the first candidate whose worst
+// label passes the unconstrained test f = ||u_k||^2 - ||z_k[:m]||^2 <= f_max.  That candidate
+// is then checked exactly: a_k = L_m^{-T} z_k[:m] and f_k = ||u_k||^2 - ||z_k||^2 - mu0 ||a_k||^2,
+// which is the squared residual ||Q_s a_k - u_k||^2 (a^T (G + mu0 I) a = z^T z = b^T a).  If some ||a_k|| > rho the constrained minimum can only be larger, and the
+// trust-region solution (Newton on 1/||a(mu)|| - 1/rho, a Cholesky of G_m + mu I per step) is
+// computed for it and, if it fails, for the following candidates.
+// ---------------------------------------------------------------------------------------
+template <int LP>
+__global__ void __launch_bounds__(256, 1)
+k_adapt(const double* __restrict__ G, int ldg, const double* __restrict__ bv, int ldb,
+        const float* __restrict__ Qs, int ldq, const float* __restrict__ Us, int ldu, int S,
+        int L, int mmax, int mstep, double rho, double fmax, int* __restrict__ mdev,
+        double* __restrict__ fsel) {
+  extern __shared__ float sm[];
+  const int ms = mmax | 1;
+  float* A = sm;                          // mmax x ms, lower factor
+  float* z = A + (size_t)mmax * ms;       // L x mmax
+  float* bb = z + (size_t)L * mmax;       // L x mmax
+  float* al = bb + (size_t)L * mmax;      // L x mmax
+  __shared__ float ck[RW_MAX_LABELS], zz[RW_MAX_LABELS], fk[RW_MAX_LABELS], nk[RW_MAX_LABELS];
+  __shared__ float dinv[kMaxSmallM];  // reciprocals of diag(L)
+  __shared__ float mu0s, red;
+  __shared__ int chosen, bad, done, capped;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  const int ncand = (mmax + mstep - 1) / mstep;
+  auto cand_m = [&](int c) { return min((c + 1) * mstep, mmax); };
+  // ||u_k||^2, mu0, right-hand sides
+  if (tid < RW_MAX_LABELS) { ck[tid] = 0.f; zz[tid] = 0.f; }
+  if (tid == 0) { chosen = -1; bad = 0; done = 0; capped = 0; }
+  __syncthreads();
+  {
+    float acc[LP];
+#pragma unroll
+    for (int k = 0; k < LP; ++k) acc[k] = 0.f;
+    for (int s = tid; s < S; s += blockDim.x)
+#pragma unroll
+      for (int k = 0; k < LP; ++k)
+        if (k < L) { float u = Us[(int64_t)s * ldu + k]; acc[k] = fmaf(u, u, acc[k]); }
+#pragma unroll
+    for (int k = 0; k < LP; ++k) {
+      float v = warp_sum(acc[k]);
+      if (lane == 0 && k < L) atomicAdd(&ck[k], v);
+    }
+  }
+  if (warp == 0) {
     double tr = 0.0;
-    for (int i = 0; i < m; ++i) tr += G[(int64_t)i * ldg + i];
-    mu0s = (float)(1e-6 * tr / m);
+    for (int i = lane; i < mmax; i += 32) tr += G[(int64_t)i * ldg + i];
+    for (int o = 16; o > 0; o >>= 1) tr += __shfl_xor_sync(0xffffffff, tr, o);
+    if (lane == 0) mu0s = (float)(1e-6 * tr / mmax);
+  }
+  for (int e = tid; e < L * mmax; e += blockDim.x) {
+    const int k = e / mmax, i = e % mmax;
+    bb[e] = (float)bv[(int64_t)i * ldb + k];
   }
   __syncthreads();
   const float mu0 = mu0s;
-  load_shifted_gram(A, m, ms, G, ldg, mu0);
-  bool ok = chol_lower_smem(A, m, ms);
-  for (int k = warp; k < L; k += nw) {
-    fwd_lower_warp(A, m, ms, bb + k * m, z + k * m);
-    bwd_lowerT_warp(A, m, ms, z + k * m, al + k * m);
-    float s = 0.f;
-    for (int i = lane; i < m; i += 32) s = fmaf(al[k * m + i], al[k * m + i], s);
-    s = warp_sum(s);
-    if (lane == 0) nrm[k] = sqrtf(s);
-  }
-  __syncthreads();
-  // labels whose minimum-norm solution leaves the ball: Newton on the secular equation
-  for (int k = 0; k < L && ok; ++k) {
-    if (!(nrm[k] > (float)rho)) continue;
-    float mu = mu0;
-    for (int it = 0; it < 40; ++it) {
-      __syncthreads();
-      float na = nrm[k];
-      if (fabsf(na - (float)rho) <= 1e-5f * (float)rho) break;
-      // q: L q = alpha, ||q||^2 = alpha^T (G + mu I)^{-1} alpha
-      if (warp == 0) {
-        fwd_lower_warp(A, m, ms, al + k * m, z + k * m);
-        float s = 0.f;
-        for (int i = lane; i < m; i += 32) s = fmaf(z[k * m + i], z[k * m + i], s);
-        s = warp_sum(s);
-        if (lane == 0) red[0] = s;
+  int rows_done = 0;
+  for (int K = 0; K * 32 < mmax; ++K) {
+    const int r0 = K * 32, nr = min(32, mmax - r0);
+    // tile row K of G + mu0 I (columns 0 .. r0 + nr)
+    for (int i = r0 + warp; i < r0 + nr; i += nw)
+      for (int j = lane; j <= i; j += 32)
+        A[i * ms + j] = (float)G[(int64_t)i * ldg + j] + (i == j ? mu0 : 0.f);
+    __syncthreads();
+    // off-diagonal tiles L_KJ = (A_KJ - sum_{t<J} L_Kt L_Jt^T) L_JJ^{-T}, J = 0..K-1 in order
+    for (int J = 0; J < K; ++J) {
+      const int c0 = J * 32;
+      // each warp owns rows r0 + warp + nw * q, q = 0..3 (32 rows / 8 warps): their
+      // dot products and triangular solves run interleaved
+      float y[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int r = r0 + warp + nw * q;
+        y[q] = (r < r0 + nr) ? A[r * ms + c0 + lane] : 0.f;
+      }
+      const float* lrow = A + (c0 + lane) * ms;
+      for (int t = 0; t < c0; ++t) {
+        const float l = lrow[t];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int r = r0 + warp + nw * q;
+          if (r < r0 + nr) y[q] = fmaf(-A[r * ms + t], l, y[q]);
+        }
+      }
+      for (int u = 0; u < 32; ++u) {
+        const float du = dinv[c0 + u];
+        const float lu = (lane > u) ? A[(c0 + lane) * ms + c0 + u] : 0.f;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          if (lane == u) y[q] *= du;
+          const float xu = __shfl_sync(0xffffffff, y[q], u);
+          if (lane > u) y[q] = fmaf(-xu, lu, y[q]);
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int r = r0 + warp + nw * q;
+        if (r < r0 + nr) A[r * ms + c0 + lane] = y[q];
       }
       __syncthreads();
-      float nq2 = red[0];
-      float step = (na * na / fmaxf(nq2, 1e-30f)) * ((na - (float)rho) / (float)rho);
-      mu = fmaxf(mu + step, mu0);
-      __syncthreads();
-      load_shifted_gram(A, m, ms, G, ldg, mu);
-      if (!chol_lower_smem(A, m, ms)) { ok = false; break; }
-      if (warp == 0) {
-        fwd_lower_warp(A, m, ms, bb + k * m, z + k * m);
-        bwd_lowerT_warp(A, m, ms, z + k * m, al + k * m);
-        float s = 0.f;
-        for (int i = lane; i < m; i += 32) s = fmaf(al[k * m + i], al[k * m + i], s);
-        s = warp_sum(s);
-        if (lane == 0) nrm[k] = sqrtf(s);
+    }
+    // diagonal tile: A_KK -= sum_{t<K} L_Kt L_Kt^T, then its Cholesky by one warp
+    for (int r = r0 + warp; r < r0 + nr; r += nw) {
+      const int c = r0 + lane;
+      if (c <= r) {
+        float y = A[r * ms + c];
+        for (int t = 0; t < r0; ++t) y = fmaf(-A[r * ms + t], A[c * ms + t], y);
+        A[r * ms + c] = y;
       }
     }
     __syncthreads();
-  }
-  // f_k = ||Q_s a_k - u_k||^2 over the seeds
-  if (threadIdx.x < RW_MAX_LABELS) fk[threadIdx.x] = 0.f;
-  __syncthreads();
-  for (int k = 0; k < L; ++k) {
-    float acc = 0.f;
-    for (int s = threadIdx.x; s < S; s += blockDim.x) {
-      const float* q = Qs + (int64_t)s * mp;
-      float r = -Us[(int64_t)s * lp + k];
-      for (int j = 0; j < m; ++j) r = fmaf(q[j], al[k * m + j], r);
-      acc = fmaf(r, r, acc);
+    if (warp == 0) chol_diag_block_warp(A, ms, r0, nr, dinv + r0, &bad);
+    __syncthreads();
+    // z_k on tile K: z = L_KK^{-1} (b_K - sum_J L_KJ z_J), one warp per label
+    for (int k = warp; k < L; k += nw) {
+      float y = 0.f;
+      if (lane < nr) {
+        y = bb[k * mmax + r0 + lane];
+        for (int t = 0; t < r0; ++t) y = fmaf(-A[(r0 + lane) * ms + t], z[k * mmax + t], y);
+      }
+      for (int u = 0; u < nr; ++u) {
+        if (lane == u) y *= dinv[r0 + u];
+        const float zu = __shfl_sync(0xffffffff, y, u);
+        if (lane > u && lane < nr) y = fmaf(-zu, A[(r0 + lane) * ms + r0 + u], y);
+      }
+      if (lane < nr) z[k * mmax + r0 + lane] = y;
+      // prefix sums of z^2 inside the tile; f_u(m) = ck - zz - prefix
+      float sq = (lane < nr) ? y * y : 0.f;
+      for (int o = 1; o < 32; o <<= 1) {
+        const float v = __shfl_up_sync(0xffffffff, sq, o);
+        if (lane >= o) sq += v;
+      }
+      // candidates inside (r0, r0 + nr]: m - r0 - 1 is the lane whose inclusive prefix applies
+      for (int c = 0; c < ncand; ++c) {
+        const int m = cand_m(c);
+        if (m <= r0 || m > r0 + nr) continue;
+        const float pre = __shfl_sync(0xffffffff, sq, m - r0 - 1);
+        if (lane == 0) al[k * mmax + c] = ck[k] - (zz[k] + pre);  // f_u(candidate c), label k
+      }
+      const float tot = __shfl_sync(0xffffffff, sq, 31);
+      if (lane == 0) zz[k] += tot;
     }
-    acc = warp_sum(acc);
-    if (lane == 0) atomicAdd(&fk[k], acc);
+    __syncthreads();
+    rows_done = r0 + nr;
+    if (tid == 0) {
+      for (int c = 0; c < ncand && chosen < 0; ++c) {
+        const int m = cand_m(c);
+        if (m <= r0 || m > r0 + nr) continue;
+        bool pass = !bad;
+        for (int k = 0; k < L; ++k)
+          if (!(al[k * mmax + c] <= (float)fmax)) pass = false;
+        if (pass) chosen = c;
+      }
+    }
+    __syncthreads();
+    if (chosen >= 0) break;
+  }
+  if (tid == 0 && chosen < 0) { chosen = ncand - 1; capped = 1; }
+  __syncthreads();
+  // exact check of the chosen candidate: a_k = L_m^{-T} z_k[:m], ||a_k||, direct residual
+  int c = chosen;
+  int m = cand_m(c);
+  // ||a_k|| from the back-substitution; f_k = ||u_k||^2 - ||z_k[:m]||^2 - mu0 ||a_k||^2, the
+  // squared residual of the (mu0-regularized) fit, since L^T a = z and L z = b.
+  for (int k = warp; k < L; k += nw) {
+    bwd_lowerT_warp_reg(A, m, ms, dinv, z + k * mmax, al + k * mmax);
+    float s2 = 0.f, zz2 = 0.f;
+    for (int i = lane; i < m; i += 32) {
+      s2 = fmaf(al[k * mmax + i], al[k * mmax + i], s2);
+      zz2 = fmaf(z[k * mmax + i], z[k * mmax + i], zz2);
+    }
+    s2 = warp_sum(s2);
+    zz2 = warp_sum(zz2);
+    if (lane == 0) {
+      nk[k] = sqrtf(s2);
+      fk[k] = ck[k] - zz2 - mu0 * s2;
+    }
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
-    bool p = ok;
-    for (int k = 0; k < L; ++k) {
-      double f = ok ? (double)fk[k] : INFINITY;
-      fout[(int64_t)blockIdx.x * lp + k] = f;
-      if (!(f <= fmax)) p = false;
+  bool inside = true;
+  for (int k = 0; k < L; ++k)
+    if (!(nk[k] <= (float)rho)) inside = false;
+  if (!inside) {
+    // trust region for candidates c, c + 1, ... (rare: the fit leaves the ball)
+    (void)rows_done;
+    for (; c < ncand; ++c) {
+      m = cand_m(c);
+      const int mss = m | 1;
+      float* B2 = A;  // reuse the factor storage: G_m + mu I, stride mss
+      float* dk = bb;  // scratch (right-hand sides are reloaded below)
+      (void)dk;
+      load_shifted_gram(B2, m, mss, G, ldg, mu0);
+      __syncthreads();
+      bool okc = chol_lower_smem(B2, m, mss);
+      for (int k = warp; k < L; k += nw) {
+        for (int i = lane; i < m; i += 32) z[k * mmax + i] = (float)bv[(int64_t)i * ldb + k];
+        __syncwarp();
+        fwd_lower_warp(B2, m, mss, z + k * mmax, z + k * mmax);
+        bwd_lowerT_warp(B2, m, mss, z + k * mmax, al + k * mmax);
+        float s2 = 0.f;
+        for (int i = lane; i < m; i += 32) s2 = fmaf(al[k * mmax + i], al[k * mmax + i], s2);
+        s2 = warp_sum(s2);
+        if (lane == 0) nk[k] = sqrtf(s2);
+      }
+      __syncthreads();
+      for (int k = 0; k < L && okc; ++k) {
+        if (!(nk[k] > (float)rho)) continue;
+        float mu = mu0;
+        for (int it = 0; it < 40; ++it) {
+          __syncthreads();
+          const float na = nk[k];
+          if (fabsf(na - (float)rho) <= 1e-5f * (float)rho) break;
+          if (warp == 0) {  // ||q||^2 with L q = a
+            fwd_lower_warp(B2, m, mss, al + k * mmax, bb + k * mmax);
+            float s2 = 0.f;
+            for (int i = lane; i < m; i += 32) s2 = fmaf(bb[k * mmax + i], bb[k * mmax + i], s2);
+            s2 = warp_sum(s2);
+            if (lane == 0) red = s2;
+          }
+          __syncthreads();
+          mu = fmaxf(mu + (na * na / fmaxf(red, 1e-30f)) * ((na - (float)rho) / (float)rho), mu0);
+          load_shifted_gram(B2, m, mss, G, ldg, mu);
+          __syncthreads();
+          if (!chol_lower_smem(B2, m, mss)) { okc = false; break; }
+          if (warp == 0) {
+            for (int i = lane; i < m; i += 32) z[k * mmax + i] = (float)bv[(int64_t)i * ldb + k];
+            __syncwarp();
+            fwd_lower_warp(B2, m, mss, z + k * mmax, z + k * mmax);
+            bwd_lowerT_warp(B2, m, mss, z + k * mmax, al + k * mmax);
+            float s2 = 0.f;
+            for (int i = lane; i < m; i += 32) s2 = fmaf(al[k * mmax + i], al[k * mmax + i], s2);
+            s2 = warp_sum(s2);
+            if (lane == 0) nk[k] = sqrtf(s2);
+          }
+        }
+        __syncthreads();
+      }
+      seed_residuals(Qs, ldq, Us, ldu, S, L, m, al, fk, mmax);
+      bool pass = okc;
+      for (int k = 0; k < L; ++k)
+        if (!(fk[k] <= (float)fmax)) pass = false;
+      if (pass) break;
+      __syncthreads();
     }
-    pass[blockIdx.x] = p ? 1 : 0;
+    if (c >= ncand) { c = ncand - 1; if (tid == 0) capped = 1; }
   }
-}
-
-__global__ void k_pick(const int* __restrict__ cand, const int* __restrict__ pass, int ncand,
-                       const double* __restrict__ fc, int lp, int* mdev, double* fsel) {
-  if (threadIdx.x != 0) return;
-  int c = ncand - 1, capped = 1;
-  for (int i = 0; i < ncand; ++i)
-    if (pass[i]) { c = i; capped = 0; break; }
-  mdev[0] = cand[c];
-  mdev[1] = capped;
-  for (int k = 0; k < lp; ++k) fsel[k] = fc[(int64_t)c * lp + k];
+  __syncthreads();
+  if (tid == 0) {
+    mdev[0] = cand_m(c);
+    mdev[1] = capped;
+    for (int k = 0; k < L; ++k) fsel[k] = fk[k];
+  }
 }
 
 __global__ void k_set_m(int* mdev, int m) {
@@ -508,178 +811,409 @@ __global__ void k_reduce_partials(const float* __restrict__ part, int nblk, int 
 // ---------------------------------------------------------------------------------------
 // Small system of Eq. (Fs) in Woodbury form, one CTA:
 //   M = diag(lambda + gamma) - K_m,  M y = h + gamma K (Lambda_gamma Z),  C = y + gamma Lambda_gamma Z
-// LU with partial pivoting in FP32 shared memory.
+// LU in FP32 shared memory.  M is diagonally dominant in practice (its off-diagonal part is
+// Q_s^T X, small next to lambda + gamma), so the elimination first runs without pivoting (one
+// barrier per step, multipliers left unscaled: l_ik = a_ik / u_kk applied on the fly).  If a
+// pivot falls below 1e-3 of its original diagonal entry, M is reloaded and eliminated with
+// partial pivoting (rows permuted through an index array, two barriers per step).
 // ---------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(1024)
-k_small_solve(const double* __restrict__ K, int ldk, const double* __restrict__ h,
+__device__ void load_M(float* M, int m, int ms, const double* __restrict__ K, int ldk,
+                       const double* __restrict__ lam, double gamma) {
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5, nty = blockDim.x >> 5;
+  for (int i = ty; i < m; i += nty)
+    for (int j = tx; j < m; j += 32) {
+      float v = -(float)K[(int64_t)i * ldk + j];
+      if (i == j) v += (float)(lam[i] + gamma);
+      M[i * ms + j] = v;
+    }
+}
+
+template <int LP>
+__global__ void __launch_bounds__(256, 1)
+k_small_solve(const double* __restrict__ K, int ldk, const double* __restrict__ h, int ldh,
               const double* __restrict__ Z, const double* __restrict__ lam, double gamma,
-              int L, int lp, int mp, const int* __restrict__ mdev, float* __restrict__ C,
+              int L, int lp, int mq, const int* __restrict__ mdev, float* __restrict__ C,
               int* status) {
   extern __shared__ float sm[];
   const int m = mdev[0];
   const int ms = m | 1;
   float* M = sm;                       // m x ms
   float* W = M + (size_t)m * ms;       // m x L : Lambda_gamma Z
-  float* B = W + (size_t)m * L;        // m x L : right-hand sides -> y
-  __shared__ int piv_row, bad;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  if (threadIdx.x == 0) bad = 0;
+  float* B = W + (size_t)m * L;        // m x L : right-hand sides
+  float* Y = B + (size_t)m * L;        // m x L : solution
+  int* perm = reinterpret_cast<int*>(Y + (size_t)m * L);  // m
+  float* invd = reinterpret_cast<float*>(perm + m);       // m
+  __shared__ int bad, unstable;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5, nty = blockDim.x >> 5;
+  const int warp = ty, lane = tx;
+  if (threadIdx.x == 0) { bad = 0; unstable = 0; }
   for (int e = threadIdx.x; e < m * L; e += blockDim.x) {
     int i = e / L, k = e % L;
     W[i * L + k] = (float)(Z[(int64_t)i * lp + k] / (lam[i] + gamma));
   }
-  for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
-    int i = e / m, j = e % m;
-    float v = -(float)K[(int64_t)i * ldk + j];
-    if (i == j) v += (float)(lam[i] + gamma);
-    M[i * ms + j] = v;
+  load_M(M, m, ms, K, ldk, lam, gamma);
+  for (int i = threadIdx.x; i < m; i += blockDim.x) {
+    perm[i] = i;
+    invd[i] = fabsf((float)(lam[i] + gamma) - (float)K[(int64_t)i * ldk + i]);  // |M_ii|
   }
   __syncthreads();
-  // B = h + gamma K W
-  for (int e = threadIdx.x; e < m * L; e += blockDim.x) {
-    int i = e / L, k = e % L;
-    float s = 0.f;
-    for (int j = 0; j < m; ++j) s = fmaf((float)K[(int64_t)i * ldk + j], W[j * L + k], s);
-    B[i * L + k] = (float)h[(int64_t)i * lp + k] + (float)gamma * s;
+  // B = h + gamma K W, with K read back from the shared copy of M (K_ij = -M_ij off the
+  // diagonal, K_ii = lambda_i + gamma - M_ii): a warp per row, lanes over the columns
+  for (int i = warp; i < m; i += nty) {
+    float acc[LP];
+#pragma unroll
+    for (int k = 0; k < LP; ++k) acc[k] = 0.f;
+    const float dii = (float)(lam[i] + gamma);
+    for (int j = lane; j < m; j += 32) {
+      const float kij = (j == i) ? dii - M[i * ms + j] : -M[i * ms + j];
+#pragma unroll
+      for (int k = 0; k < LP; ++k)
+        if (k < L) acc[k] = fmaf(kij, W[j * L + k], acc[k]);
+    }
+#pragma unroll
+    for (int k = 0; k < LP; ++k) {
+      const float sk = warp_sum(acc[k]);
+      if (lane == 0 && k < L) B[i * L + k] = (float)h[(int64_t)i * ldh + k] + (float)gamma * sk;
+    }
   }
-  // LU with partial pivoting
+  // elimination without pivoting
   for (int k = 0; k < m; ++k) {
-    __syncthreads();
-    if (warp == 0) {
-      float best = -1.f;
-      int bi = k;
-      for (int i = k + lane; i < m; i += 32) {
-        float a = fabsf(M[i * ms + k]);
-        if (a > best) { best = a; bi = i; }
-      }
-      for (int o = 16; o > 0; o >>= 1) {
-        float ob = __shfl_xor_sync(0xffffffff, best, o);
-        int oi = __shfl_xor_sync(0xffffffff, bi, o);
-        if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
-      }
-      if (lane == 0) {
-        piv_row = bi;
-        if (!(best > 0.f)) bad = 1;
+    float pv = M[k * ms + k];
+    if (!(fabsf(pv) >= 1e-3f * invd[k])) {
+      if (threadIdx.x == 0) unstable = 1;
+      pv = (pv == 0.f) ? 1e-30f : pv;
+    }
+    const float inv = 1.f / pv;
+    float rowk[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      const int j = k + 1 + tx + 32 * c;
+      rowk[c] = (j < m) ? M[k * ms + j] : 0.f;
+    }
+    for (int i = k + 1 + ty; i < m; i += nty) {
+      const float a = M[i * ms + k] * inv;
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        const int j = k + 1 + tx + 32 * c;
+        if (j < m) M[i * ms + j] = fmaf(-a, rowk[c], M[i * ms + j]);
       }
     }
     __syncthreads();
-    const int p = piv_row;
-    if (p != k) {
-      for (int j = threadIdx.x; j < m; j += blockDim.x) {
-        float t = M[k * ms + j]; M[k * ms + j] = M[p * ms + j]; M[p * ms + j] = t;
-      }
-      for (int j = threadIdx.x; j < L; j += blockDim.x) {
-        float t = B[k * L + j]; B[k * L + j] = B[p * L + j]; B[p * L + j] = t;
+  }
+  if (unstable) {
+    // partial pivoting from the original M
+    __syncthreads();
+    load_M(M, m, ms, K, ldk, lam, gamma);
+    for (int k = 0; k < m; ++k) {
+      __syncthreads();
+      if (warp == 0) {  // pivot among the rows perm[k..m-1]
+        float best = -1.f;
+        int bi = k;
+        for (int i = k + lane; i < m; i += 32) {
+          float a = fabsf(M[perm[i] * ms + k]);
+          if (a > best) { best = a; bi = i; }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+          float ob = __shfl_xor_sync(0xffffffff, best, o);
+          int oi = __shfl_xor_sync(0xffffffff, bi, o);
+          if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+        }
+        if (lane == 0) {
+          if (!(best > 0.f)) bad = 1;
+          int t = perm[k]; perm[k] = perm[bi]; perm[bi] = t;
+        }
       }
       __syncthreads();
+      const int pk = perm[k];
+      float pv = M[pk * ms + k];
+      if (pv == 0.f) pv = 1e-30f;
+      const float inv = 1.f / pv;
+      for (int r = k + 1 + ty; r < m; r += nty) {
+        const int pr = perm[r];
+        const float a = M[pr * ms + k] * inv;
+        for (int j = k + 1 + tx; j < m; j += 32) M[pr * ms + j] = fmaf(-a, M[pk * ms + j], M[pr * ms + j]);
+      }
     }
-    float pv = M[k * ms + k];
-    if (pv == 0.f) pv = 1e-30f;
-    const float inv = 1.f / pv;
-    const int w = m - k - 1;
-    for (int i = k + 1 + threadIdx.x; i < m; i += blockDim.x) M[i * ms + k] *= inv;
     __syncthreads();
-    for (int e = threadIdx.x; e < w * w; e += blockDim.x) {
-      int i = k + 1 + e / w, j = k + 1 + e % w;
-      M[i * ms + j] = fmaf(-M[i * ms + k], M[k * ms + j], M[i * ms + j]);
-    }
   }
+  for (int i = threadIdx.x; i < m; i += blockDim.x) invd[i] = 1.f / M[perm[i] * ms + i];
   __syncthreads();
-  // forward (unit lower) and backward (upper) substitution, one warp per label
-  for (int k = warp; k < L; k += nw) {
-    for (int i = 0; i < m; ++i) {
-      float s = 0.f;
-      for (int j = lane; j < i; j += 32) s = fmaf(M[i * ms + j], B[j * L + k], s);
-      s = warp_sum(s);
-      if (lane == 0) B[i * L + k] -= s;
+  // forward (unit lower, multipliers a_ij / u_jj) and backward (upper) substitution, column
+  // oriented, one warp per label
+  for (int k = warp; k < L; k += nty) {
+    for (int i = lane; i < m; i += 32) Y[i * L + k] = B[perm[i] * L + k];
+    __syncwarp();
+    for (int j = 0; j < m; ++j) {
+      const float f = Y[j * L + k] * invd[j];
+      for (int i = j + 1 + lane; i < m; i += 32) Y[i * L + k] = fmaf(-M[perm[i] * ms + j], f, Y[i * L + k]);
       __syncwarp();
     }
     for (int i = m - 1; i >= 0; --i) {
-      float s = 0.f;
-      for (int j = i + 1 + lane; j < m; j += 32) s = fmaf(M[i * ms + j], B[j * L + k], s);
-      s = warp_sum(s);
-      if (lane == 0) B[i * L + k] = (B[i * L + k] - s) / M[i * ms + i];
+      const float yi = Y[i * L + k] * invd[i];
+      __syncwarp();
+      if (lane == 0) Y[i * L + k] = yi;
+      for (int j = lane; j < i; j += 32) Y[j * L + k] = fmaf(-M[perm[j] * ms + i], yi, Y[j * L + k]);
       __syncwarp();
     }
   }
   __syncthreads();
-  for (int e = threadIdx.x; e < mp * lp; e += blockDim.x) {
+  for (int e = threadIdx.x; e < mq * lp; e += blockDim.x) {
     int i = e / lp, k = e % lp;
     float v = 0.f;
-    if (i < m && k < L) v = B[i * L + k] + (float)gamma * W[i * L + k];
+    if (i < m && k < L) v = Y[i * L + k] + (float)gamma * W[i * L + k];
     C[e] = v;
   }
   if (threadIdx.x == 0 && bad) atomicOr(status, RW_DEV_SINGULAR);
 }
 
 // ---------------------------------------------------------------------------------------
-// U-hat_n = Q_n C.  Same thread mapping as k_project; per-(row, chunk) partial dot products
-// go to shared memory and are summed per row.  Writes either the refinement start (hat
-// space, seeds = d^{1/2} one-hot) or the final U / labels.
+// U-hat_n = Q_n C on the row-major FP32 basis.  One warp per group of RB rows (RB = 16 / LP, so every warp iteration
+// produces 16 (row, label) sums); lane c holds chunk c of each row and the matching rows of C
+// in registers.  The 16 partial sums are reduced across the warp by a reduce-scatter
+// butterfly (each exchange halves the values a lane keeps; 16 shuffles in all), after which
+// the even lane 2j holds sum j = (row j / LP, label j % LP).  Writes either the refinement
+// start (hat space, seeds = d^{1/2} one-hot) or the final U / labels.
 // ---------------------------------------------------------------------------------------
-template <typename T, int LP>
-__global__ void __launch_bounds__(1024)
-k_backproject(const T* __restrict__ Q, int ldq, int cpr, int R, const float* __restrict__ Cg,
+template <typename T, int LP, int CPL>
+__global__ void __launch_bounds__(256)
+k_backproject(const T* __restrict__ Q, int ldq, int cpr, const float* __restrict__ Cg,
               float cscale, const int* __restrict__ seedlab, const float* __restrict__ sq,
               const float* __restrict__ s, int64_t N, int L, const int* __restrict__ mdev,
               float* __restrict__ xhat, float* __restrict__ U, uint8_t* __restrict__ labels) {
   constexpr int V = Vec16<T>::V;
-  extern __shared__ float smem[];
-  float* Cs = smem;                    // ldq x LP
-  float* part = Cs + ldq * LP;         // R x cpr x LP
-  const int c = threadIdx.x % cpr, r = threadIdx.x / cpr;
+  constexpr int RB = 16 / LP;  // rows per warp iteration
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int m = mdev[0];
-  for (int e = threadIdx.x; e < ldq * LP; e += blockDim.x) Cs[e] = Cg[e] * cscale;
-  __syncthreads();
-  const bool active = r < R && c * V < m;
-  for (int64_t base = (int64_t)blockIdx.x * R; base < N; base += (int64_t)gridDim.x * R) {
-    const int64_t i = base + r;
-    if (r < R) {
+  float creg[CPL][V][LP];
+#pragma unroll
+  for (int t = 0; t < CPL; ++t) {
+    const int c = lane + 32 * t;
+#pragma unroll
+    for (int v = 0; v < V; ++v)
+#pragma unroll
+      for (int k = 0; k < LP; ++k)
+        creg[t][v][k] = (c < cpr) ? __ldg(Cg + (c * V + v) * LP + k) * cscale : 0.f;
+  }
+  const int64_t ngroups = (N + RB - 1) / RB;
+  for (int64_t grp = (int64_t)blockIdx.x * nw + warp; grp < ngroups;
+       grp += (int64_t)gridDim.x * nw) {
+    const int64_t i0 = grp * RB;
+    float val[16];
+#pragma unroll
+    for (int r = 0; r < RB; ++r) {
+      const int64_t i = i0 + r;
       float acc[LP];
 #pragma unroll
       for (int k = 0; k < LP; ++k) acc[k] = 0.f;
-      if (active && i < N) {
-        float q[V];
-        Vec16<T>::load(Q + i * ldq + c * V, q);
+      if (i < N) {
 #pragma unroll
-        for (int v = 0; v < V; ++v)
+        for (int t = 0; t < CPL; ++t) {
+          const int c = lane + 32 * t;
+          if (c < cpr && c * V < m) {
+            float q[V];
+            Vec16<T>::load(Q + i * ldq + c * V, q);
 #pragma unroll
-          for (int k = 0; k < LP; ++k) acc[k] = fmaf(q[v], Cs[(c * V + v) * LP + k], acc[k]);
-      }
+            for (int v = 0; v < V; ++v)
 #pragma unroll
-      for (int k = 0; k < LP; ++k) part[(r * cpr + c) * LP + k] = acc[k];
-    }
-    __syncthreads();
-    for (int e = threadIdx.x; e < R * LP; e += blockDim.x) {
-      int rr = e / LP, k = e % LP;
-      int64_t ii = base + rr;
-      if (ii >= N) continue;
-      float v = 0.f;
-      for (int cc = 0; cc < cpr; ++cc) v += part[(rr * cpr + cc) * LP + k];
-      int sl = seedlab[ii];
-      if (sl >= 0) v = (k == sl) ? sq[ii] : 0.f;
-      if (k >= L) v = 0.f;
-      if (xhat) {
-        xhat[ii * LP + k] = v;
-      } else if (k < L) {
-        U[ii * L + k] = (sl >= 0) ? ((k == sl) ? 1.f : 0.f) : v * s[ii];
-      }
-    }
-    if (!xhat && labels) {
-      __syncthreads();
-      for (int rr = threadIdx.x; rr < R; rr += blockDim.x) {
-        int64_t ii = base + rr;
-        if (ii >= N) continue;
-        int best = 0;
-        float bv = U[ii * L];
-        for (int k = 1; k < L; ++k) {
-          float v = U[ii * L + k];
-          if (v > bv) { bv = v; best = k; }
+              for (int k = 0; k < LP; ++k) acc[k] = fmaf(q[v], creg[t][v][k], acc[k]);
+          }
         }
-        labels[ii] = (uint8_t)best;
+      }
+#pragma unroll
+      for (int k = 0; k < LP; ++k) val[r * LP + k] = acc[k];
+    }
+    // reduce-scatter: 16 -> 8 -> 4 -> 2 -> 1 values per lane, then the last pair
+#pragma unroll
+    for (int half = 8, off = 16; half >= 1; half >>= 1, off >>= 1) {
+      const bool up = (lane & off) != 0;
+#pragma unroll
+      for (int t = 0; t < half; ++t) {
+        const float send = up ? val[t] : val[t + half];
+        const float keep = up ? val[t + half] : val[t];
+        val[t] = keep + __shfl_xor_sync(0xffffffff, send, off);
       }
     }
-    __syncthreads();
+    const float sum = val[0] + __shfl_xor_sync(0xffffffff, val[0], 1);
+    // even lane 2j holds entry j = r * LP + k
+    const int j = lane >> 1;
+    const int r = j / LP, k = j % LP;
+    const int64_t i = i0 + r;
+    const bool writer = (lane & 1) == 0 && i < N;
+    int sl = -1;
+    if (writer) sl = seedlab[i];
+    if (xhat) {
+      if (writer) xhat[i * LP + k] = (k >= L) ? 0.f : ((sl >= 0) ? (k == sl ? sq[i] : 0.f) : sum);
+    } else {
+      float u = 0.f;
+      if (writer && k < L) {
+        u = (sl >= 0) ? (k == sl ? 1.f : 0.f) : sum * s[i];
+        U[i * L + k] = u;
+      }
+      if (labels) {
+        // lanes 2 (r LP + k), k = 0..LP-1, hold row r: argmax over the first L, ties -> lowest
+        int best = 0;
+        float bv = __shfl_sync(0xffffffff, u, (lane & ~(2 * LP - 1)));
+        for (int kk = 1; kk < LP; ++kk) {
+          const float o = __shfl_sync(0xffffffff, u, (lane & ~(2 * LP - 1)) + 2 * kk);
+          if (kk < L && o > bv) { bv = o; best = kk; }
+        }
+        if (writer && k == 0) labels[i] = (uint8_t)best;
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// 16-bit basis copies are stored panel-major: for each 8-column chunk c an N x 8 panel of
+// 16-byte rows, element (i, 8c + v) at ((c N + i) 8 + v).  Using the first m columns reads the
+// first ceil(m / 8) panels end to end.
+// ---------------------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ void load8(const T* p, float* o) { Vec16<T>::load(p, o); }
+
+// Z = Q_n^T P-hat_n on the panel layout: lane = row (32 consecutive rows per warp step), the
+// 8 x LP products of one chunk are reduced across the warp by a reduce-scatter butterfly and
+// accumulated per warp in shared memory; warps are summed in a fixed order into per-block
+// partials.
+template <typename T, int LP>
+__global__ void __launch_bounds__(256)
+k_project_panel(const T* __restrict__ Qp, int64_t N, int nchunk_max,
+                const float* __restrict__ phat, const int* __restrict__ seedlab,
+                const int* __restrict__ mdev, float* __restrict__ part) {
+  constexpr int NV = 8 * LP;       // products per row and chunk
+  constexpr int NG = NV / 32;      // groups of 32 reduced at once
+  extern __shared__ float red[];   // nw x (nchunk_max * NV)
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int m = mdev[0];
+  const int nch = min((m + 7) / 8, nchunk_max);
+  float* wred = red + (size_t)warp * nchunk_max * NV;
+  for (int e = lane; e < nchunk_max * NV; e += 32) wred[e] = 0.f;
+  __syncwarp();
+  const int64_t ngrp = (N + 31) / 32;
+  for (int64_t gI = (int64_t)blockIdx.x * nw + warp; gI < ngrp; gI += (int64_t)gridDim.x * nw) {
+    const int64_t i = gI * 32 + lane;
+    float p[LP];
+    bool use = false;
+    if (i < N) use = __ldg(seedlab + i) < 0;
+    if (use) {
+#pragma unroll
+      for (int k4 = 0; k4 < LP / 4; ++k4) {
+        float4 pv = __ldg(reinterpret_cast<const float4*>(phat + i * LP) + k4);
+        p[4 * k4] = pv.x; p[4 * k4 + 1] = pv.y; p[4 * k4 + 2] = pv.z; p[4 * k4 + 3] = pv.w;
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < LP; ++k) p[k] = 0.f;
+    }
+    for (int c = 0; c < nch; ++c) {
+      float q[8];
+      if (use) {
+        load8<T>(Qp + ((int64_t)c * N + i) * 8, q);
+      } else {
+#pragma unroll
+        for (int v = 0; v < 8; ++v) q[v] = 0.f;
+      }
+#pragma unroll
+      for (int gq = 0; gq < NG; ++gq) {
+        float val[32];
+#pragma unroll
+        for (int t = 0; t < 32; ++t) {
+          const int j = gq * 32 + t;
+          val[t] = q[j / LP] * p[j % LP];
+        }
+#pragma unroll
+        for (int half = 16, off = 16; half >= 1; half >>= 1, off >>= 1) {
+          const bool up = (lane & off) != 0;
+#pragma unroll
+          for (int t = 0; t < half; ++t) {
+            const float send = up ? val[t] : val[t + half];
+            const float keep = up ? val[t + half] : val[t];
+            val[t] = keep + __shfl_xor_sync(0xffffffff, send, off);
+          }
+        }
+        wred[c * NV + gq * 32 + lane] += val[0];  // lane holds product index gq*32 + lane
+      }
+    }
+  }
+  __syncthreads();
+  // block partial: sum the warps in order; entry (col = 8c + v, k) at col * LP + k
+  for (int e = threadIdx.x; e < nchunk_max * NV; e += blockDim.x) {
+    float s = 0.f;
+    for (int w = 0; w < nw; ++w) s += red[(size_t)w * nchunk_max * NV + e];
+    // e = c * NV + j, j = v * LP + k  ->  (8c + v) * LP + k = e
+    part[(int64_t)blockIdx.x * nchunk_max * NV + e] = s;
+  }
+}
+
+// U-hat_n = Q_n C on the panel layout: lane = row, the chunk's 8 x LP coefficients come from
+// shared memory as broadcasts; no cross-lane reduction.
+template <typename T, int LP>
+__global__ void __launch_bounds__(256)
+k_backproject_panel(const T* __restrict__ Qp, int64_t N, int nchunk_max,
+                    const float* __restrict__ Cg, float cscale, const int* __restrict__ seedlab,
+                    const float* __restrict__ sq, const float* __restrict__ s, int L,
+                    const int* __restrict__ mdev, float* __restrict__ xhat,
+                    float* __restrict__ U, uint8_t* __restrict__ labels) {
+  extern __shared__ float Cs[];  // (8 nchunk_max) x LP
+  const int m = mdev[0];
+  const int nch = min((m + 7) / 8, nchunk_max);
+  for (int e = threadIdx.x; e < nchunk_max * 8 * LP; e += blockDim.x) Cs[e] = Cg[e] * cscale;
+  __syncthreads();
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int sl = __ldg(seedlab + i);
+    float acc[LP];
+#pragma unroll
+    for (int k = 0; k < LP; ++k) acc[k] = 0.f;
+    if (sl < 0) {
+      int c = 0;
+      for (; c + 2 <= nch; c += 2) {  // two chunks in flight
+        float q0[8], q1[8];
+        load8<T>(Qp + ((int64_t)c * N + i) * 8, q0);
+        load8<T>(Qp + ((int64_t)(c + 1) * N + i) * 8, q1);
+#pragma unroll
+        for (int v = 0; v < 8; ++v)
+#pragma unroll
+          for (int k = 0; k < LP; ++k) {
+            acc[k] = fmaf(q0[v], Cs[(c * 8 + v) * LP + k], acc[k]);
+            acc[k] = fmaf(q1[v], Cs[((c + 1) * 8 + v) * LP + k], acc[k]);
+          }
+      }
+      if (c < nch) {
+        float q0[8];
+        load8<T>(Qp + ((int64_t)c * N + i) * 8, q0);
+#pragma unroll
+        for (int v = 0; v < 8; ++v)
+#pragma unroll
+          for (int k = 0; k < LP; ++k) acc[k] = fmaf(q0[v], Cs[(c * 8 + v) * LP + k], acc[k]);
+      }
+    }
+    if (xhat) {
+      float4* xo = reinterpret_cast<float4*>(xhat + i * LP);
+#pragma unroll
+      for (int k4 = 0; k4 < LP / 4; ++k4) {
+        float o[4];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+          const int k = 4 * k4 + t;
+          o[t] = (k >= L) ? 0.f : ((sl >= 0) ? (k == sl ? sq[i] : 0.f) : acc[k]);
+        }
+        xo[k4] = make_float4(o[0], o[1], o[2], o[3]);
+      }
+    } else {
+      const float si = s[i];
+      int best = 0;
+      float bv = -INFINITY;
+#pragma unroll
+      for (int k = 0; k < LP; ++k) {
+        if (k < L) {
+          const float u = (sl >= 0) ? (k == sl ? 1.f : 0.f) : acc[k] * si;
+          U[i * L + k] = u;
+          if (u > bv) { bv = u; best = k; }
+        }
+      }
+      if (labels) labels[i] = (uint8_t)best;
+    }
   }
 }
 
@@ -751,10 +1285,13 @@ k_jacobi_step(const float* __restrict__ xin, float* __restrict__ xout,
   const float si = s[i];
   int best = 0;
   float bv = -INFINITY;
-  for (int k = 0; k < L; ++k) {
-    float u = (sl >= 0) ? (k == sl ? 1.f : 0.f) : xv[k] * si;
-    U[i * L + k] = u;
-    if (u > bv) { bv = u; best = k; }
+#pragma unroll
+  for (int k = 0; k < LP; ++k) {
+    if (k < L) {
+      const float u = (sl >= 0) ? (k == sl ? 1.f : 0.f) : xv[k] * si;
+      U[i * L + k] = u;
+      if (u > bv) { bv = u; best = k; }
+    }
   }
   if (labels) labels[i] = (uint8_t)best;
 }
@@ -788,8 +1325,21 @@ rw_status launch_proj_back(bool back, const T* Q, int ldq, const float* phat,
                            uint8_t* labels, int L, cudaStream_t st) {
   constexpr int V = Vec16<T>::V;
   const int cpr = ldq / V;
-  const int R = std::max(1, 1024 / cpr);
-  const int threads = cpr * R;
+  if constexpr (V == 8) {  // 16-bit copies: panel-major layout, ldq = 8 x chunks
+    const int nchunk = ldq / 8;
+    if (!back) {
+      const size_t shm = sizeof(float) * 8 * (size_t)nchunk * 8 * LP;
+      if (shm > 48 * 1024)
+        cudaFuncSetAttribute(k_project_panel<T, LP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+      k_project_panel<T, LP><<<nblk, 256, shm, st>>>(Q, g->N, nchunk, phat, seedlab, mdev, part);
+    } else {
+      const size_t shm = sizeof(float) * (size_t)nchunk * 8 * LP;
+      k_backproject_panel<T, LP><<<nblk, 256, shm, st>>>(Q, g->N, nchunk, C, cscale, seedlab,
+                                                        g->sq, g->s, L, mdev, xhat, U, labels);
+    }
+    RW_LAUNCH_CHECK();
+    return RW_OK;
+  } else {
   if (!back) {
     size_t shm = sizeof(float) * ldq * LP;
     if (cpr <= 32)
@@ -799,14 +1349,18 @@ rw_status launch_proj_back(bool back, const T* Q, int ldq, const float* phat,
     else
       return RW_ERR_UNSUPPORTED;
   } else {
-    size_t shm = sizeof(float) * ((size_t)ldq * LP + (size_t)R * cpr * LP);
-    if (shm > 48 * 1024)
-      cudaFuncSetAttribute(k_backproject<T, LP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
-    k_backproject<T, LP><<<nblk, threads, shm, st>>>(Q, ldq, cpr, R, C, cscale, seedlab, g->sq,
-                                                     g->s, g->N, L, mdev, xhat, U, labels);
+    if (cpr <= 32)
+      k_backproject<T, LP, 1><<<nblk, 256, 0, st>>>(Q, ldq, cpr, C, cscale, seedlab, g->sq, g->s,
+                                                   g->N, L, mdev, xhat, U, labels);
+    else if (cpr <= 64)
+      k_backproject<T, LP, 2><<<nblk, 256, 0, st>>>(Q, ldq, cpr, C, cscale, seedlab, g->sq, g->s,
+                                                   g->N, L, mdev, xhat, U, labels);
+    else
+      return RW_ERR_UNSUPPORTED;
   }
   RW_LAUNCH_CHECK();
   return RW_OK;
+  }
 }
 
 template <typename T>
@@ -820,13 +1374,14 @@ rw_status proj_back(int lp, bool back, const T* Q, int ldq, const float* phat, c
   }
 }
 
+// BF16 copy in the panel-major layout of the 16-bit basis copies
 __global__ void k_f32_to_bf16(const float* __restrict__ a, int64_t N, int m, int lda,
                               __nv_bfloat16* __restrict__ b, int ldb) {
   int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= N * ldb) return;
   int64_t r = e / ldb;
-  int c = (int)(e % ldb);
-  b[e] = __float2bfloat16(c < m ? a[r * lda + c] : 0.f);
+  int col = (int)(e % ldb);
+  b[((int64_t)(col / 8) * N + r) * 8 + (col % 8)] = __float2bfloat16(col < m ? a[r * lda + col] : 0.f);
 }
 
 }  // namespace
@@ -889,7 +1444,8 @@ static rw_status validate_solve(const rw_graph* g, const rw_basis* b, const int3
   if (mmax > kMaxSmallM) return RW_ERR_UNSUPPORTED;
   // one CTA holds an m x m FP32 matrix plus label-sized vectors in shared memory
   const size_t shm_adapt = sizeof(float) * ((size_t)mmax * (mmax | 1) + 3 * (size_t)L * mmax);
-  const size_t shm_small = sizeof(float) * ((size_t)mmax * (mmax | 1) + 2 * (size_t)L * mmax);
+  const size_t shm_small = sizeof(float) * ((size_t)mmax * (mmax | 1) + 3 * (size_t)L * mmax + mmax) +
+                           sizeof(int) * mmax;
   if (std::max(o->m == 0 ? shm_adapt : 0, shm_small) > 227 * 1024) return RW_ERR_UNSUPPORTED;
   return RW_OK;
 }
@@ -918,16 +1474,11 @@ extern "C" rw_status rw_solve(const rw_graph* g, const rw_basis* b, const int32_
   const bool adaptive = opts->m == 0;
   const int m_max = adaptive ? b->m : opts->m;
   // adaptive candidates: m_step, 2 m_step, ..., m_max (m_max last)
-  int cand_h[2048];
-  int ncand = 0;
-  if (adaptive) {
-    for (int m = m_step; m < m_max && ncand < 2047; m += m_step) cand_h[ncand++] = m;
-    cand_h[ncand++] = m_max;
-  }
+  const int ncand = adaptive ? (m_max + m_step - 1) / m_step : 0;
   const int sms = g_rw_num_sms > 0 ? g_rw_num_sms : 148;
   const int nblk = 4 * sms;  // blocks of the two basis passes (partials of the projection)
   const int mq = std::max(b->ld16, b->ld32);  // rows of Z, C and the partials
-  Layout lay = make_layout(S, mp, mq, lp, std::max(ncand, 1), nblk);
+  Layout lay = make_layout(S, mp, mq, lp, L, std::max(ncand, 1), nblk);
   RW_TRY(ws.small.grow(lay.total));
   char* base = ws.small.as<char>();
   auto P = [&](size_t off) { return base + off; };
@@ -950,40 +1501,42 @@ extern "C" rw_status rw_solve(const rw_graph* g, const rw_basis* b, const int32_
                                   priors_dev, lp, st, &phat, &seedlab, &fit64));
 
   RW_TRY(mark(1));
-  float* Qs = reinterpret_cast<float*>(P(lay.Qs));
-  float* Xs = reinterpret_cast<float*>(P(lay.Xs));
-  float* Us = reinterpret_cast<float*>(P(lay.Us));
-  float* R0 = reinterpret_cast<float*>(P(lay.R0));
+  const int wcat = 2 * mp + 2 * lp;
+  float* Bcat = reinterpret_cast<float*>(P(lay.Bcat));
+  double* Gcat = reinterpret_cast<double*>(P(lay.Gcat));
+  float* Qs = Bcat + mp;               // S x m_max, row pitch wcat
+  float* Us = Bcat + 2 * mp + lp;      // S x lp
+  double* K = Gcat;                    // Q_s^T X
+  double* G = Gcat + mp;               // Q_s^T Q_s
+  double* h = Gcat + 2 * mp;           // Q_s^T r0
+  double* bv = Gcat + 2 * mp + lp;     // Q_s^T U-hat_s
   k_seed_gather<<<rw_blocks((int64_t)S * 32, 256), 256, 0, st>>>(
       seed_idx_dev, seed_lab_dev, S, L, lp, g->N, b->Q32, b->ld32, mp, seedlab, g->cw, g->d,
       g->sq, g->normalized, g->kind, g->ndim, g->dims[0], g->dims[1], g->dims[2], g->rowptr,
-      g->col, g->ccsr, (float)gamma, Qs, Xs, Us, R0);
+      g->col, g->ccsr, (float)gamma, Bcat, wcat);
   RW_LAUNCH_CHECK();
-  double* G = reinterpret_cast<double*>(P(lay.G));
-  double* K = reinterpret_cast<double*>(P(lay.K));
-  double* bv = reinterpret_cast<double*>(P(lay.bv));
-  double* h = reinterpret_cast<double*>(P(lay.h));
-  RW_TRY(rw_gram(Qs, mp, Xs, mp, S, m_max, m_max, K, mp, false, st));
-  RW_TRY(rw_gram(Qs, mp, R0, lp, S, m_max, lp, h, lp, false, st));
-  double* fsel = reinterpret_cast<double*>(P(lay.fc)) + (size_t)ncand * lp;
-  if (adaptive) {
-    RW_TRY(rw_gram(Qs, mp, Qs, mp, S, m_max, m_max, G, mp, false, st));
-    RW_TRY(rw_gram(Qs, mp, Us, lp, S, m_max, lp, bv, lp, false, st));
-  }
+  RW_TRY(rw_gram(Qs, wcat, Bcat, wcat, S, m_max, wcat, Gcat, wcat, false, st));
+  double* fu = reinterpret_cast<double*>(P(lay.fu));
+  double* fsel = fu + (size_t)(ncand + 1) * RW_MAX_LABELS;
   RW_TRY(mark(2));
   if (adaptive) {
-    int* cand = reinterpret_cast<int*>(P(lay.cand));
-    int* pass = reinterpret_cast<int*>(P(lay.pass));
-    double* fc = reinterpret_cast<double*>(P(lay.fc));
-    RW_CHECK_CUDA(cudaMemcpyAsync(cand, cand_h, sizeof(int) * ncand, cudaMemcpyHostToDevice, st));
-    // rho = sqrt(1^T D 1) (normalized, Sec. III-A-1) or sqrt(N): needs the degree sum
+    // rho = sqrt(1^T D 1) with the normalized Laplacian (Sec. III-A-1), else sqrt(N)
     const double rho = g->normalized ? sqrt(g->dsum) : sqrt((double)g->N);
     const double fmax = (double)S * eps * eps;
-    size_t shm = sizeof(float) * ((size_t)m_max * (m_max | 1) + 3 * (size_t)L * m_max);
-    cudaFuncSetAttribute(k_adapt, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
-    k_adapt<<<ncand, 1024, shm, st>>>(G, mp, bv, lp, Qs, mp, Us, S, L, cand, rho, fmax, fc, pass);
-    RW_LAUNCH_CHECK();
-    k_pick<<<1, 32, 0, st>>>(cand, pass, ncand, fc, lp, mdev, fsel);
+    const size_t shm = sizeof(float) * ((size_t)m_max * (m_max | 1) + 3 * (size_t)L * m_max);
+    if (lp == 4) {
+      cudaFuncSetAttribute(k_adapt<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+      k_adapt<4><<<1, 256, shm, st>>>(G, wcat, bv, wcat, Qs, wcat, Us, wcat, S, L, m_max, m_step,
+                                      rho, fmax, mdev, fsel);
+    } else if (lp == 8) {
+      cudaFuncSetAttribute(k_adapt<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+      k_adapt<8><<<1, 256, shm, st>>>(G, wcat, bv, wcat, Qs, wcat, Us, wcat, S, L, m_max, m_step,
+                                      rho, fmax, mdev, fsel);
+    } else {
+      cudaFuncSetAttribute(k_adapt<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+      k_adapt<16><<<1, 256, shm, st>>>(G, wcat, bv, wcat, Qs, wcat, Us, wcat, S, L, m_max, m_step,
+                                       rho, fmax, mdev, fsel);
+    }
     RW_LAUNCH_CHECK();
   } else {
     k_set_m<<<1, 32, 0, st>>>(mdev, m_max);
@@ -1016,9 +1569,21 @@ extern "C" rw_status rw_solve(const rw_graph* g, const rw_basis* b, const int32_
   // small system
   float* C = reinterpret_cast<float*>(P(lay.C));
   {
-    size_t shm = sizeof(float) * ((size_t)m_max * (m_max | 1) + 2 * (size_t)L * m_max);
-    cudaFuncSetAttribute(k_small_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
-    k_small_solve<<<1, 1024, shm, st>>>(K, mp, h, Z, b->lam, gamma, L, lp, mq, mdev, C, g->status);
+    size_t shm = sizeof(float) * ((size_t)m_max * (m_max | 1) + 3 * (size_t)L * m_max + m_max) +
+                 sizeof(int) * m_max;
+    if (lp == 4) {
+      cudaFuncSetAttribute(k_small_solve<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+      k_small_solve<4><<<1, 256, shm, st>>>(K, wcat, h, wcat, Z, b->lam, gamma, L, lp, mq, mdev, C,
+                                            g->status);
+    } else if (lp == 8) {
+      cudaFuncSetAttribute(k_small_solve<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+      k_small_solve<8><<<1, 256, shm, st>>>(K, wcat, h, wcat, Z, b->lam, gamma, L, lp, mq, mdev, C,
+                                            g->status);
+    } else {
+      cudaFuncSetAttribute(k_small_solve<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+      k_small_solve<16><<<1, 256, shm, st>>>(K, wcat, h, wcat, Z, b->lam, gamma, L, lp, mq, mdev,
+                                             C, g->status);
+    }
     RW_LAUNCH_CHECK();
   }
   RW_TRY(mark(5));
