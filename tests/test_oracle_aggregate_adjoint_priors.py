@@ -4,7 +4,7 @@ import pytest
 import scipy.sparse as sp
 
 import synth
-from oracle import adjoint, aggregate, eig, exact, graph, priors
+from oracle import adjoint, aggregate, eig, exact, fastrw, graph, priors, refine, update
 
 
 def _graph(dims=(8, 8), seed=0, beta=30.0):
@@ -84,6 +84,46 @@ def test_exact_gradient_matches_central_differences(normalized):
     fd = adjoint.fd_grad(loss_of, g, pos, h_beta=1e-4, h_rel=1e-4)
     np.testing.assert_allclose(gb, fd["beta"], rtol=1e-6)
     np.testing.assert_allclose(gw[pos], fd["edges"], rtol=1e-5, atol=1e-9)
+
+
+def _fast_case(m=14):
+    g, si, sl, P, truth = _grad_case()
+    lam, Q = np.linalg.eigh(g.Lhat.toarray())
+    return g, si, sl, P, truth, Q[:, :m]
+
+
+def test_fast_forward_equals_pipeline_pieces():
+    """The forward kept for the fast-path adjoint is the fast solve (Eqs. Fs, U_lin_comb) plus
+    the damped-Jacobi refinement, as composed from the separate oracle pieces."""
+    g, si, sl, P, truth, Q = _fast_case()
+    lam = update.updated_values(g, Q)
+    U1, _ = adjoint.fast_forward(g, Q, lam, si, sl, 2, P, 0.05, refine_steps=3, omega=0.8)
+    U0 = fastrw.fast_rw(g, Q, lam, si, sl, 2, P, 0.05)
+    U2, _ = refine.refine(g, U0, si, sl, 2, P, 0.05, 3, True, "jacobi", 0.8)
+    np.testing.assert_allclose(U1, U2, atol=1e-12)
+
+
+@pytest.mark.parametrize("steps", [0, 3])
+def test_fast_gradient_matches_central_differences(steps):
+    """Reverse-mode gradient of the fast path (Q fixed, values by Eq. z_ray under the changed
+    weights) against central differences of the pipeline pieces, on every edge and beta."""
+    g, si, sl, P, truth, Q = _fast_case()
+    gamma = 0.05
+
+    def loss_of(gg):
+        lam = update.updated_values(gg, Q)
+        U = fastrw.fast_rw(gg, Q, lam, si, sl, 2, P, gamma)
+        if steps:
+            U, _ = refine.refine(gg, U, si, sl, 2, P, gamma, steps, True, "jacobi", 0.8)
+        return adjoint.mask_loss(U, truth, si)[0]
+    lam = update.updated_values(g, Q)
+    U, _ = adjoint.fast_forward(g, Q, lam, si, sl, 2, P, gamma, steps, 0.8)
+    _, G = adjoint.mask_loss(U, truth, si)
+    gw, gb, _ = adjoint.fast_grad(g, Q, si, sl, 2, P, gamma, G, refine_steps=steps, omega=0.8)
+    fd = adjoint.fd_grad(loss_of, g, np.arange(g.ids.size), h_beta=1e-5, h_rel=1e-5)
+    np.testing.assert_allclose(gb, fd["beta"], rtol=2e-6)
+    scale = np.abs(fd["edges"]).max()
+    assert np.abs(gw - fd["edges"]).max() <= 2e-6 * scale
 
 
 def test_gaussian_priors_match_normal_pdf():
