@@ -38,7 +38,7 @@ extern "C" {
 typedef enum rw_status {
   RW_OK = 0,
   RW_WARN_M_CAPPED = 1,          /* adaptive m: no candidate met f <= f_max; m_max was used   */
-  RW_WARN_NOT_CONVERGED = 2,     /* eigensolver stopped at max_iter; basis returned anyway     */
+  RW_WARN_NOT_CONVERGED = 2,     /* an iteration stopped at max_iter; its result is returned   */
   RW_ERR_INVALID_ARG = -1,       /* bad sizes, null pointers, seed/label out of range, dups    */
   RW_ERR_CUDA = -2,              /* a CUDA runtime call failed                                 */
   RW_ERR_OOM = -3,               /* device allocation of scratch memory failed                 */
@@ -273,7 +273,10 @@ rw_status rw_update_topology(rw_graph* g, rw_basis* b, const rw_topology_update*
  *   d loss / d beta = sum_e (d loss / d w_e) (d w_e / d beta).
  * U_dev must be the converged exact solution (e.g. rw_solve_pcg with a tight tol) and
  * priors_dev the priors it used (N x n_labels, e.g. from rw_solve_priors).
- * grad_w_dev: ndim * N floats in edge-id layout (0 where no edge).  grad_beta_host: 1 double.
+ * grad_w_dev: ndim * N floats in edge-id layout (0 where no edge).  grad_beta_host: 1 double
+ * (may be NULL).  Grid graphs only (RW_ERR_UNSUPPORTED for an aggregate's CSR graph); gamma > 0.
+ * Returns RW_WARN_NOT_CONVERGED (gradients still written) when the adjoint PCG used max_iter
+ * iterations.  Uses the graph's solve scratch (not concurrently with rw_solve on g).
  * Synchronizes.
  * ---------------------------------------------------------------------------------------- */
 rw_status rw_grad_exact(const rw_graph* g, const int32_t* seed_idx_dev,
