@@ -223,7 +223,7 @@ rw_status rw_solve_pcg(const rw_graph* g, const int32_t* seed_idx_dev,
  * become lambda-hat_i = q_i^T L-hat_new q_i, evaluated as the edge sum
  * sum_e w_e (q_i(a) d_a^{-1/2} - q_i(b) d_b^{-1/2})^2.
  * ---------------------------------------------------------------------------------------- */
-enum { RW_UPDATE_BETA = 0, RW_UPDATE_EDGES = 1, RW_UPDATE_ROI = 2 };
+enum { RW_UPDATE_BETA = 0, RW_UPDATE_EDGES = 1, RW_UPDATE_ROI = 2, RW_UPDATE_ALL = 3 };
 
 typedef struct rw_weight_update {
   int32_t kind;               /* RW_UPDATE_*                                                 */
@@ -232,13 +232,16 @@ typedef struct rw_weight_update {
   int32_t roi_lo[3];          /* ROI: half-open box [lo, hi) per axis; edges with both ends   */
   int32_t roi_hi[3];          /*      inside are recomputed from Eq. (W)                      */
   const int64_t* edge_ids_dev;/* EDGES: n_edges distinct edge ids                             */
-  const float* edge_w_dev;    /* EDGES: their new weights (>= 0)                              */
+  const float* edge_w_dev;    /* EDGES: their new weights (>= 0); ALL: ndim * N weights in    */
+                              /*      edge-id layout (slots without an edge are ignored)       */
   int64_t n_edges;
 } rw_weight_update;
 
-/* Mutates the graph's weights and the basis values in place (basis must belong to g).  The
- * ROI and EDGES kinds update the values incrementally from the edges whose contribution
- * changed.  RW_ERR_ISOLATED_NODE if a degree becomes 0.  Synchronizes. */
+/* Mutates the graph's weights and the basis values in place (basis must belong to g, or
+ * NULL to change the weights only).  The ROI and EDGES kinds update the values incrementally
+ * from the edges whose contribution changed; BETA and ALL recompute every value (Eq. z_ray).
+ * RW_ERR_ISOLATED_NODE if a degree becomes 0; RW_ERR_INVALID_ARG (via the device status) for a
+ * negative or non-finite weight in ALL.  Synchronizes. */
 rw_status rw_update_weights(rw_graph* g, rw_basis* b, const rw_weight_update* u, void* stream);
 
 enum { RW_TOPO_REMOVE_EDGES = 0, RW_TOPO_AGGREGATE = 1 };
@@ -284,6 +287,31 @@ rw_status rw_grad_exact(const rw_graph* g, const int32_t* seed_idx_dev,
                         const float* priors_dev, double gamma, const float* U_dev,
                         const float* dloss_dU_dev, double rel_tol, int32_t max_iter,
                         float* grad_w_dev, double* grad_beta_host, void* stream);
+
+/* ------------------------------------------------------------------------------------------
+ * Gradient through the eigenvector solve (Sec. II-B, normalized form of Sec. II-C; not in the
+ * paper, derived from its equations).  The first m columns of the basis are held fixed and
+ * their values are the Rayleigh quotients of Eq. (z_ray) under the graph's current weights
+ * (as after rw_precompute or rw_update_weights).  The forward is the fast solve at fixed m
+ * (Eqs. Fs, U_lin_comb, in the m x m Woodbury form) followed by refine_steps damped-Jacobi
+ * steps with factor omega on (L-hat_n + gamma I) U-hat_n = gamma P-hat_n - B-hat^T U-hat_s,
+ * computed from the FP32 basis; the reverse pass differentiates every step, including the
+ * values lambda-hat(w), the coefficients w_ab d_a^{-1/2} d_b^{-1/2} and the degrees, down to
+ * the edge weights and beta (Eq. W).
+ *   priors_dev: N x n_labels probabilities (e.g. from rw_solve_priors); held fixed.
+ *   dloss_dU_dev: N x n_labels, d loss / d U (seeded rows ignored).
+ *   U_out_dev: N x n_labels forward result, or NULL.
+ *   grad_w_dev: ndim * N floats in edge-id layout (0 where no edge); grad_beta_host may be NULL.
+ * Normalized grid graphs only (RW_ERR_UNSUPPORTED otherwise); gamma > 0; 1 <= m <= basis m,
+ * m <= 1024; 0 < omega <= 1.  RW_ERR_SINGULAR if the m x m system has a zero pivot.
+ * Scratch: grown inside the graph handle on first use (about (refine_steps + 7) N n_pad + 2 ndim N
+ * floats, n_pad = 4/8/16).  Synchronizes.
+ * ---------------------------------------------------------------------------------------- */
+rw_status rw_grad_fast(const rw_graph* g, const rw_basis* b, const int32_t* seed_idx_dev,
+                       const int32_t* seed_lab_dev, int32_t S, int32_t n_labels,
+                       const float* priors_dev, double gamma, int32_t m, int32_t refine_steps,
+                       double omega, const float* dloss_dU_dev, float* U_out_dev,
+                       float* grad_w_dev, double* grad_beta_host, void* stream);
 
 /* ------------------------------------------------------------------------------------------
  * Rayleigh quotients of caller columns with no device allocation.  The paper has no

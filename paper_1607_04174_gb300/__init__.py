@@ -229,6 +229,16 @@ def rw_grad_exact(g, seed_idx, seed_lab, n_labels, priors, gamma, U, dloss_dU, g
     return gb.value
 
 
+def rw_grad_fast(g, b, seed_idx, seed_lab, n_labels, priors, gamma, m, dloss_dU, grad_w,
+                 refine_steps=3, omega=0.8, U_out=None, stream=None):
+    gb = C.c_double(0.0)
+    _check(abi.lib().rw_grad_fast(g, b, _p(seed_idx), _p(seed_lab), len(seed_idx), n_labels,
+                                  _p(priors), gamma, m, refine_steps, omega, _p(dloss_dU),
+                                  _p(U_out), _p(grad_w), C.byref(gb), _stream(stream)),
+           "rw_grad_fast")
+    return gb.value
+
+
 def rw_solve_priors(g, seed_idx, seed_lab, n_labels, priors, stream=None):
     return _check(abi.lib().rw_solve_priors(g, _p(seed_idx), _p(seed_lab), len(seed_idx),
                                             n_labels, _p(priors), _stream(stream)),

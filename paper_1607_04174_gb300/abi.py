@@ -28,7 +28,7 @@ RW_REFINE_JACOBI, RW_REFINE_PCG = 0, 1
 RW_BASIS_F16, RW_BASIS_BF16, RW_BASIS_F32 = 0, 1, 2
 RW_MAX_LABELS = 16
 RW_NOALLOC_MAX_M = 1024
-RW_UPDATE_BETA, RW_UPDATE_EDGES, RW_UPDATE_ROI = 0, 1, 2
+RW_UPDATE_BETA, RW_UPDATE_EDGES, RW_UPDATE_ROI, RW_UPDATE_ALL = 0, 1, 2, 3
 RW_TOPO_REMOVE_EDGES, RW_TOPO_AGGREGATE = 0, 1
 RW_PHASES = ("seeds", "gather", "adapt", "project", "small", "back", "refine")
 
@@ -102,6 +102,7 @@ PROTOTYPES = {
     "rw_update_weights": (I32, [P, P, C.POINTER(rw_weight_update), P]),
     "rw_update_topology": (I32, [P, P, C.POINTER(rw_topology_update), P, HP, HP]),
     "rw_grad_exact": (I32, [P, P, P, I32, I32, P, D, P, P, D, I32, P, C.POINTER(D), P]),
+    "rw_grad_fast": (I32, [P, P, P, P, I32, I32, P, D, I32, I32, D, P, P, P, C.POINTER(D), P]),
     "rw_solve_priors": (I32, [P, P, P, I32, I32, P, P]),
     "rw_rayleigh_quotients_noalloc": (I32, [P, P, I64, I32, P, P]),
 }

@@ -309,7 +309,7 @@ static void graph_release(rw_graph* g) {
   cudaFree(g->sq); cudaFree(g->status); cudaFree(g->rowptr); cudaFree(g->col);
   cudaFree(g->wcsr); cudaFree(g->ccsr);
   g->ws.seedlab.release(); g->ws.small.release(); g->ws.xhat[0].release();
-  g->ws.xhat[1].release(); g->ws.phat.release(); g->ws.pcg.release(); g->ws.stage.release(); g->ws.host.release();
+  g->ws.xhat[1].release(); g->ws.phat.release(); g->ws.pcg.release(); g->ws.stage.release(); g->ws.grad.release(); g->ws.host.release();
   for (auto& e : g->ws.ev) if (e) cudaEventDestroy(e);
   g->upd.release();
   delete g;
@@ -393,6 +393,42 @@ extern "C" rw_status rw_apply_laplacian(const rw_graph* g, const float* X_dev, i
   if (rw_round_up(k, 4) > ldx || rw_round_up(k, 4) > ldy) return RW_ERR_INVALID_ARG;
   return rw_stencil_apply(g, X_dev, ldx, Y_dev, ldy, k, 1.f, 0.f, nullptr, 0, 0.f,
                           rw_stream(stream));
+}
+
+// every weight from a caller array in edge-id layout (slots without an edge are ignored and
+// stored as 0); a negative or non-finite weight sets RW_DEV_NONFINITE
+__global__ void k_set_all_weights(const float* __restrict__ src, int64_t N, int ndim, int X,
+                                  int Y, int Z, float* __restrict__ w, int* status) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= ndim * N) return;
+  const int a = (int)(e / N);
+  const int64_t i = e % N;
+  const int c = a == 0 ? (int)(i % X) : (a == 1 ? (int)((i / X) % Y) : (int)(i / ((int64_t)X * Y)));
+  const int n = a == 0 ? X : (a == 1 ? Y : Z);
+  float v = 0.f;
+  if (c + 1 < n) {
+    v = src[e];
+    if (!(v >= 0.f) || !isfinite(v)) { atomicOr(status, RW_DEV_NONFINITE); v = 0.f; }
+  }
+  w[e] = v;
+}
+
+rw_status rw_set_all_weights(rw_graph* g, const float* w_dev, cudaStream_t st) {
+  if (g->kind != RW_GRAPH_GRID || !w_dev) return RW_ERR_INVALID_ARG;
+  k_set_all_weights<<<rw_blocks(g->ndim * g->N, 256), 256, 0, st>>>(
+      w_dev, g->N, g->ndim, g->dims[0], g->dims[1], g->dims[2], g->w, g->status);
+  RW_LAUNCH_CHECK();
+  k_degree_from_w<<<rw_blocks(g->N, 256), 256, 0, st>>>(g->w, g->N, g->ndim, g->dims[0],
+                                                        g->dims[1], g->dims[2], g->normalized,
+                                                        nullptr, g->d, g->s, g->sq, g->status);
+  RW_LAUNCH_CHECK();
+  RW_TRY(rw_graph_coeffs(g, st));
+  int bits = 0;
+  RW_CHECK_CUDA(cudaMemcpyAsync(&bits, g->status, sizeof(int), cudaMemcpyDeviceToHost, st));
+  RW_CHECK_CUDA(cudaMemsetAsync(g->status, 0, sizeof(int), st));
+  RW_CHECK_CUDA(cudaStreamSynchronize(st));
+  if (bits) return rw_status_from_device_bits(bits);
+  return rw_graph_degree_sum(g, st);
 }
 
 // new beta for every edge: weights, degrees, scalings, coefficients, degree sum

@@ -71,6 +71,7 @@ struct SolveWorkspace {
   DevBuf phat;      // hat-space priors, N x lpad FP32
   DevBuf pcg;       // PCG vectors
   DevBuf stage;     // device staging of the host-buffer entry point
+  DevBuf grad;      // fast-path gradient scratch (grown on first use)
   PinnedBuf host;   // info readback
   cudaEvent_t ev[8] = {};  // phase timing events (created on first use)
   int64_t small_cap_S = 0, small_cap_m = 0;
@@ -135,6 +136,8 @@ rw_status rw_stencil_apply(const rw_graph* g, const float* X, int64_t ldx, float
 rw_status rw_graph_coeffs(rw_graph* g, cudaStream_t st);
 rw_status rw_graph_degree_sum(rw_graph* g, cudaStream_t st);  // sets g->dsum, synchronizes
 rw_status rw_graph_reserve_scratch(rw_graph* g);
+// every edge weight from an ndim x N edge-id array; degrees, scalings, coefficients (syncs)
+rw_status rw_set_all_weights(rw_graph* g, const float* w_dev, cudaStream_t st);
 
 // dense.cu (small / tall-skinny dense helpers)
 // G (p x q, row-major, ldg, FP64) = (accumulate ? G : 0) + A^T B, A: N x p (lda), B: N x q (ldb)

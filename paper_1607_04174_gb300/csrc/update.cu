@@ -518,6 +518,11 @@ extern "C" rw_status rw_update_weights(rw_graph* g, rw_basis* b, const rw_weight
       return edges_update(g, b, u->edge_ids_dev, u->edge_w_dev, u->n_edges, st);
     case RW_UPDATE_ROI:
       return roi_update(g, b, u->roi_lo, u->roi_hi, u->beta, st);
+    case RW_UPDATE_ALL:
+      if (!u->edge_w_dev || g->kind != RW_GRAPH_GRID) return RW_ERR_INVALID_ARG;
+      RW_TRY(rw_set_all_weights(g, u->edge_w_dev, st));
+      if (b) RW_TRY(rw_basis_rayleigh(g, b, st));
+      return RW_OK;
   }
   return RW_ERR_INVALID_ARG;
 }

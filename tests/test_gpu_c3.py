@@ -1,0 +1,209 @@
+"""GPU parity on the full 128^3 volume (6-connected, 2,097,152 voxels, m = 100, 2 labels, 500
+seeds per label): the eigenvector basis is certified by FP64 residuals and orthonormality (the
+oracle does not solve this eigenproblem); the online solve is compared with the oracle pipeline
+run on the same basis; the box-shaped weight change and the edge removal of Sec. III-B with the
+oracle's values; the adjoints (exact and eigenvector path) with central differences of GPU
+solves along beta and along a direction over the region-of-interest edges."""
+import time
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import adaptive, adjoint, graph, pipeline, update
+from tests.gpu_common import TOL_PROB, dev, f32, gap_mask, to_dev
+
+pytestmark = pytest.mark.gpu
+
+rw = pytest.importorskip("paper_1607_04174_gb300")
+torch = pytest.importorskip("torch")
+
+BETA, GAMMA, M, SEEDS = 90.0, 1e-3, 100, 500
+SEED = synth.BASE_SEED + 2
+
+
+@pytest.fixture(scope="module")
+def c3():
+    from paper_1607_04174_gb300 import build
+    build.build()
+    J, dims, truth = synth.ellipsoid_volume(128, seed=SEED)
+    J = f32(J)
+    si, sl = synth.sample_seeds(truth, dims, SEEDS, 2, seed=SEED)
+    go = graph.build_graph(J, dims, BETA)
+    gg = rw.rw_build_graph(to_dev(J, torch.float32), dims, BETA)
+    t0 = time.time()
+    b, info = rw.rw_precompute(gg, M, seed=3)
+    t_pre = time.time() - t0
+    N = go.N
+    Qd = torch.empty(N, M, device=dev())
+    lam = rw.rw_basis_get(b, Qd)
+    Q = Qd.cpu().numpy().astype(np.float64)
+    yield dict(J=J, dims=dims, truth=truth, si=si, sl=sl, go=go, gg=gg, b=b, info=info,
+               t_pre=t_pre, Q=Q, Qd=Qd, lam=lam, N=N)
+    rw.rw_basis_free(b)
+    rw.rw_graph_free(gg)
+
+
+def test_c3_basis_certificate(c3):
+    Q, lam, go = c3["Q"], c3["lam"], c3["go"]
+    assert c3["info"]["converged"] == M, c3["info"]
+    print(f"precompute 128^3 m={M}: {c3['t_pre']:.1f} s, {c3['info']}")
+    assert np.all(np.diff(lam) >= -1e-12)
+    assert abs(lam[0]) <= 1e-5
+    np.testing.assert_allclose(Q.T @ Q, np.eye(M), atol=2e-5)
+    LQ = go.Lhat @ Q
+    R = LQ - Q * lam
+    assert np.linalg.norm(R, axis=0).max() <= 2e-5
+    # stored values are the Rayleigh quotients of the stored columns (Eq. z_ray)
+    rq = np.einsum("ij,ij->j", Q, LQ) / np.einsum("ij,ij->j", Q, Q)
+    assert np.all(np.abs(lam - rq) <= 1e-6 * np.maximum(np.abs(rq), 1e-3))
+
+
+def test_c3_online_solve_matches_oracle_same_basis(c3):
+    N, si, sl = c3["N"], c3["si"], c3["sl"]
+    U = torch.empty(N, 2, device=dev())
+    lab = torch.empty(N, dtype=torch.uint8, device=dev())
+    _, info = rw.rw_solve(c3["gg"], c3["b"], to_dev(si), to_dev(sl), 2, U, labels=lab,
+                          gamma=GAMMA, m=0, m_step=10, eps=0.1, refine_steps=3)
+    m_gpu = info["m_used"]
+    # adaptive m: the oracle's choice agrees, or the GPU's candidate sits on the threshold
+    m_o, f_o, capped_o, table = adaptive.choose_m_from_seeds(c3["go"], c3["Q"], si, sl, 2, M,
+                                                             10, 0.1)
+    if m_o != m_gpu:
+        fmax = len(si) * 0.1 ** 2
+        edge = min(m_o, m_gpu)
+        assert abs(table[edge].max() - fmax) / fmax < 1e-3, (m_o, m_gpu)
+    ref = pipeline.online_solve(c3["go"], c3["Q"], c3["lam"], si, sl, 2, gamma=GAMMA, m=m_gpu,
+                                refine_steps=3)
+    Ug = U.cpu().numpy().astype(np.float64)
+    err = np.abs(Ug - ref["U"]).max()
+    print(f"128^3 solve: m={m_gpu} (oracle {m_o}), max |dU| = {err:.2e}")
+    assert err <= TOL_PROB
+    mask = gap_mask(ref["U"])
+    assert np.array_equal(lab.cpu().numpy()[mask], ref["labels"][mask])
+
+
+def test_c3_roi_update_then_edge_removal(c3):
+    dims, go, Q = c3["dims"], c3["go"], c3["Q"]
+    center = synth.boundary_voxel(c3["truth"], dims, seed=SEED)
+    lo, hi = synth.roi_box(center, 32, dims)
+    gg = rw.rw_build_graph(to_dev(c3["J"], torch.float32), dims, BETA)
+    b = rw.rw_basis_create(gg, c3["Qd"], c3["lam"])
+    try:
+        rw.rw_update_weights(gg, b, rw.RW_UPDATE_ROI, beta=2 * BETA, roi_lo=lo, roi_hi=hi)
+        g2 = update.update_roi(go, lo, hi, 2 * BETA)
+        np.testing.assert_allclose(rw.rw_basis_get(b), update.updated_values(g2, Q),
+                                   rtol=2e-5, atol=1e-9)
+        ids = synth.pick_edges(synth.roi_edge_ids(dims, lo, hi), 0.01, seed=SEED)
+        assert ids.size == 952
+        rw.rw_update_topology(gg, b, rw.RW_TOPO_REMOVE_EDGES, edge_ids=to_dev(ids.astype(np.int64)))
+        g3 = update.remove_edges(g2, ids)
+        np.testing.assert_allclose(rw.rw_basis_get(b), update.updated_values(g3, Q),
+                                   rtol=2e-5, atol=1e-9)
+        w = torch.empty(3 * go.N, device=dev())
+        rw.rw_graph_weights(gg, w)
+        np.testing.assert_allclose(w.cpu().numpy(), g3.weights_by_id(), rtol=2e-5, atol=1e-30)
+    finally:
+        rw.rw_basis_free(b)
+        rw.rw_graph_free(gg)
+
+
+def _priors(c3):
+    N = c3["N"]
+    P = torch.empty(N, 2, device=dev())
+    rw.rw_solve_priors(c3["gg"], to_dev(c3["si"]), to_dev(c3["sl"]), 2, P)
+    return P
+
+
+def _loss(U, truth, free):
+    d = U[free, 1].astype(np.float64) - truth[free]
+    return float(d @ d), d
+
+
+def test_c3_exact_adjoint_matches_differences(c3):
+    dims, N, si, sl = c3["dims"], c3["N"], c3["si"], c3["sl"]
+    truth = c3["truth"].astype(np.float64)
+    free = np.ones(N, bool)
+    free[si] = False
+    P = _priors(c3)
+    sid, sld = to_dev(si), to_dev(sl)
+    gg = rw.rw_build_graph(to_dev(c3["J"], torch.float32), dims, BETA)
+    try:
+        U = torch.empty(N, 2, device=dev())
+
+        def solve():
+            rw.rw_solve_pcg(gg, sid, sld, 2, U, priors=P, gamma=GAMMA, prior_mode=1,
+                            iters=20000, tol=1e-6)
+            return _loss(U.cpu().numpy(), truth, free)
+        L0, d = solve()
+        G = np.zeros((N, 2), np.float32)
+        G[free, 1] = 2 * d
+        gw = torch.empty(3 * N, device=dev())
+        gb = rw.rw_grad_exact(gg, sid, sld, 2, P, GAMMA, U, to_dev(G), gw, rel_tol=1e-6,
+                              max_iter=20000)
+        gw = gw.cpu().numpy().astype(np.float64)
+        # beta
+        h = 1.0
+        rw.rw_update_weights(gg, None, rw.RW_UPDATE_BETA, beta=BETA + h)
+        Lp, _ = solve()
+        rw.rw_update_weights(gg, None, rw.RW_UPDATE_BETA, beta=BETA - h)
+        Lm, _ = solve()
+        fd = (Lp - Lm) / (2 * h)
+        print(f"128^3 exact d loss/d beta: adjoint {gb:.6e}, differences {fd:.6e}")
+        assert abs(gb - fd) <= 3e-2 * abs(fd)
+        # direction v = sign(grad) on the ROI-internal edges, relative steps w (1 +- t v)
+        rw.rw_update_weights(gg, None, rw.RW_UPDATE_BETA, beta=BETA)
+        center = synth.boundary_voxel(c3["truth"], dims, seed=SEED)
+        lo, hi = synth.roi_box(center, 32, dims)
+        ids = synth.roi_edge_ids(dims, lo, hi)
+        w0 = c3["go"].weights_by_id()
+        v = np.zeros(3 * N)
+        v[ids] = np.sign(gw[ids])
+        t = 1e-3
+        rw.rw_update_weights(gg, None, rw.RW_UPDATE_ALL, edge_w=to_dev(w0 * (1 + t * v), torch.float32))
+        Lp, _ = solve()
+        rw.rw_update_weights(gg, None, rw.RW_UPDATE_ALL, edge_w=to_dev(w0 * (1 - t * v), torch.float32))
+        Lm, _ = solve()
+        fd_dir = (Lp - Lm) / (2 * t)
+        an_dir = float(np.sum(gw * w0 * v))
+        print(f"128^3 exact directional derivative (ROI edges): adjoint {an_dir:.6e}, "
+              f"differences {fd_dir:.6e}")
+        assert abs(an_dir - fd_dir) <= 3e-2 * abs(fd_dir)
+    finally:
+        rw.rw_graph_free(gg)
+
+
+def test_c3_fast_adjoint_beta_matches_differences(c3):
+    dims, N, si, sl = c3["dims"], c3["N"], c3["si"], c3["sl"]
+    truth = c3["truth"].astype(np.float64)
+    free = np.ones(N, bool)
+    free[si] = False
+    P = _priors(c3)
+    sid, sld = to_dev(si), to_dev(sl)
+    gg = rw.rw_build_graph(to_dev(c3["J"], torch.float32), dims, BETA)
+    b = rw.rw_basis_create(gg, c3["Qd"], c3["lam"])
+    try:
+        U = torch.empty(N, 2, device=dev())
+
+        def solve(beta):
+            rw.rw_update_weights(gg, b, rw.RW_UPDATE_BETA, beta=beta)
+            rw.rw_solve(gg, b, sid, sld, 2, U, priors=P, gamma=GAMMA, m=M, refine_steps=3,
+                        basis_format=rw.RW_BASIS_F32, prior_mode=1, want_info=False)
+            return _loss(U.cpu().numpy(), truth, free)
+        L0, d = solve(BETA)
+        G = np.zeros((N, 2), np.float32)
+        G[free, 1] = 2 * d
+        gw = torch.empty(3 * N, device=dev())
+        Uf = torch.empty(N, 2, device=dev())
+        gb = rw.rw_grad_fast(gg, b, sid, sld, 2, P, GAMMA, M, to_dev(G), gw, refine_steps=3,
+                             omega=0.8, U_out=Uf)
+        assert (Uf - U).abs().max().item() <= 1e-4
+        h = 1.0
+        Lp, _ = solve(BETA + h)
+        Lm, _ = solve(BETA - h)
+        fd = (Lp - Lm) / (2 * h)
+        print(f"128^3 fast d loss/d beta: adjoint {gb:.6e}, differences {fd:.6e}")
+        assert abs(gb - fd) <= 3e-2 * abs(fd)
+    finally:
+        rw.rw_basis_free(b)
+        rw.rw_graph_free(gg)
