@@ -32,6 +32,35 @@ void rw_count_launch();
   } while (0)
 
 void rw_set_last_cuda_error(cudaError_t e, const char* what, const char* file, int line);
+
+// Programmatic dependent launch.  A kernel launched with RW_LAUNCH may be scheduled while its
+// predecessor in the stream is still running: it must call rw_grid_wait() before it reads
+// anything an earlier kernel writes (the wait returns once the predecessor has completed and
+// its memory is visible; it returns at once for a kernel launched without the attribute).
+// rw_grid_trigger() lets the successor begin launching; it orders nothing.
+__device__ __forceinline__ void rw_grid_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void rw_grid_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+static inline cudaError_t rw_launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block,
+                                        size_t smem, cudaStream_t st, Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+#define RW_LAUNCH(kernel, grid, block, smem, st, ...)                                  \
+  do {                                                                                 \
+    RW_CHECK_CUDA(rw_launch_pdl(kernel, dim3(grid), dim3(block), smem, st, __VA_ARGS__)); \
+    rw_count_launch();                                                                 \
+  } while (0)
 void rw_set_error_message(const char* msg);
 
 // Device status word bits (ORed by kernels, read by the host).

@@ -20,8 +20,12 @@
 //   refinement steps, U = s * U-hat, labels = argmax                 -> k_jacobi_step
 #include "rw_internal.cuh"
 
+#include <cooperative_groups.h>
+
 #include <algorithm>
 #include <cstring>
+
+namespace cg = cooperative_groups;
 
 namespace {
 
@@ -42,8 +46,8 @@ Layout make_layout(int S, int mp, int mq, int lp, int L, int ncand, int nblk_par
   const size_t wcat = 2 * (size_t)mp + 2 * (size_t)lp;
   o.mdev = take(sizeof(int) * 8);
   o.Bcat = take(sizeof(float) * (size_t)S * wcat);
-  o.Gcat = take(sizeof(double) * (size_t)mp * wcat);
-  o.Z = take(sizeof(double) * (size_t)mq * lp);
+  o.Gcat = take(sizeof(float) * (size_t)mp * wcat);
+  o.Z = take(sizeof(float) * (size_t)mq * lp + sizeof(float) * (size_t)mq);  // Z, lambda + gamma
   o.C = take(sizeof(float) * (size_t)mq * lp);
   o.fu = take(sizeof(double) * (size_t)(ncand + 1) * RW_MAX_LABELS + sizeof(double) * lp);
   o.nrm = take(sizeof(float) * (size_t)(ncand + 1) * RW_MAX_LABELS);
@@ -63,15 +67,21 @@ __device__ __forceinline__ float warp_sum(float v) {
 }
 
 // ---------------------------------------------------------------------------------------
-__global__ void k_fill_i32(int* p, int64_t n, int v) {
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) p[i] = v;
+__global__ void k_seed_reset(int* __restrict__ seedlab, int64_t n, double* __restrict__ stats,
+                             int nstats) {
+  rw_grid_wait();
+  rw_grid_trigger();
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) seedlab[i] = -1;
+  if (i < nstats) stats[i] = 0.0;
 }
 
 __global__ void k_seed_scatter(const int32_t* __restrict__ idx, const int32_t* __restrict__ lab,
                                int S, int L, int64_t N, const float* __restrict__ J,
                                int* __restrict__ seedlab, double* __restrict__ stats,
                                int* status) {
+  rw_grid_wait();
+  rw_grid_trigger();
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= S) return;
   int i = idx[t], k = lab[t];
@@ -93,6 +103,8 @@ __global__ void k_seed_scatter(const int32_t* __restrict__ idx, const int32_t* _
 // mu_k, 1/(2 sigma_k^2), log sigma_k with sigma_k = max(std, 1e-3) (ML estimates, Sec. IV-A)
 __global__ void k_fit(const double* __restrict__ stats, int L, int prior_mode,
                       float* __restrict__ fit, double* __restrict__ fit64, int* status) {
+  rw_grid_wait();
+  rw_grid_trigger();
   int k = threadIdx.x;
   if (k >= L) return;
   double n = stats[3 * k + 2];
@@ -116,6 +128,8 @@ __global__ void k_fit(const double* __restrict__ stats, int L, int prior_mode,
 __global__ void k_priors(const float* __restrict__ J, const float* __restrict__ sq, int64_t N,
                          int L, int lp, int prior_mode, const float* __restrict__ fit,
                          const float* __restrict__ Pin, float* __restrict__ phat, int* status) {
+  rw_grid_wait();
+  rw_grid_trigger();
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
   float p[RW_MAX_LABELS];
@@ -150,6 +164,8 @@ __global__ void k_seed_gather(const int32_t* __restrict__ idx, const int32_t* __
                               int DX, int DY, int DZ, const int32_t* __restrict__ rowptr,
                               const int32_t* __restrict__ colv, const float* __restrict__ ccsr,
                               float gamma, float* __restrict__ Bcat, int ldb) {
+  rw_grid_wait();
+  rw_grid_trigger();
   const int lane = threadIdx.x & 31;
   const int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (t >= S) return;
@@ -199,36 +215,240 @@ __global__ void k_seed_gather(const int32_t* __restrict__ idx, const int32_t* __
 // Shared-memory FP32 dense kernels for one CTA (row stride ms, odd, so column walks are free
 // of bank conflicts).
 // ---------------------------------------------------------------------------------------
-// Cholesky of the kb x kb diagonal block at (k0, k0) by one warp in shared memory: lane r owns
-// row r; step kk uses the unscaled column (l_rc = a_r,kk a_c,kk / a_kk,kk), then the column is
-// scaled in one pass.  A compact loop (no unrolling: this runs once per tile on one warp).
-// dinv[0..kb) receives 1 / L_ii.
-__device__ void chol_diag_block_warp(float* A, int ms, int k0, int kb, float* dinv, int* bad) {
-  const int lane = threadIdx.x & 31;
-  float* T = A + k0 * ms + k0;
-  for (int kk = 0; kk < kb; ++kk) {
-    float piv = T[kk * ms + kk];
-    if (!(piv > 0.f)) piv = 1e-30f;
-    const float inv = 1.f / piv;
-    if (lane > kk && lane < kb) {
-      const float a = T[lane * ms + kk] * inv;
-      for (int c = kk + 1; c <= lane; ++c) T[lane * ms + c] = fmaf(-a, T[c * ms + kk], T[lane * ms + c]);
+// A[i][j] -= sum_{q < kb} A[i][p0 + q] A[p0 + q][j] for i, j in [r1, m): warp tasks of 8 rows x
+// 128 columns (lane = column within each 32-column group), k unrolled by 2 for ILP
+__device__ void gemm_trailing(float* A, int ms, int m, int r1, int p0, int kb) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int n = m - r1;
+  const int nrt = (n + 7) / 8, nct = (n + 127) / 128;
+  for (int task = warp; task < nrt * nct; task += nw) {
+    const int i0 = r1 + 8 * (task / nct), j0 = r1 + 128 * (task % nct) + lane;
+    float acc[8][4];
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+#pragma unroll
+      for (int v = 0; v < 4; ++v) acc[u][v] = 0.f;
+    const int ilast = m - 1;
+#pragma unroll 2
+    for (int q = 0; q < kb; ++q) {
+      float av[8], bv[4];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) av[u] = A[min(i0 + u, ilast) * ms + p0 + q];
+#pragma unroll
+      for (int v = 0; v < 4; ++v) bv[v] = A[(p0 + q) * ms + min(j0 + 32 * v, ilast)];
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(av[u], bv[v], acc[u][v]);
     }
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        const int i = i0 + u, j = j0 + 32 * v;
+        if (i < m && j < m) A[i * ms + j] -= acc[u][v];
+      }
+  }
+}
+
+// one warp: x = U^{-1} L^{-1} b for the LU held in A (unit lower below the diagonal, U on and
+// above it; uinv = 1 / diag(U)).  Lane t keeps entries t + 32 q (m <= 224) in registers; each
+// newly final entry is broadcast by shuffle.  The register group of the pivot is a
+// compile-time index (outer loop unrolled over groups), so a step is one shuffle and a few
+// independent FMAs.
+template <int QJ>
+__device__ __forceinline__ void lu_fwd_group(const float* A, int m, int ms, float (&y)[7], int lane) {
+  if (32 * QJ < m) {
+    const int jend = min(32, m - 32 * QJ);
+    for (int lj = 0; lj < jend; ++lj) {
+      const int j = 32 * QJ + lj;
+      const float yj = __shfl_sync(0xffffffff, y[QJ], lj);
+#pragma unroll
+      for (int q = QJ; q < 7; ++q) {
+        const int i = lane + 32 * q;
+        if (i > j && i < m) y[q] = fmaf(-A[i * ms + j], yj, y[q]);
+      }
+    }
+  }
+}
+template <int QI>
+__device__ __forceinline__ void lu_bwd_group(const float* A, int m, int ms, const float* uinv,
+                                             float (&y)[7], int lane) {
+  if (32 * QI < m) {
+    for (int li = min(31, m - 1 - 32 * QI); li >= 0; --li) {
+      const int i = 32 * QI + li;
+      const float xi = __shfl_sync(0xffffffff, y[QI], li) * uinv[i];
+      if (lane == li) y[QI] = xi;
+#pragma unroll
+      for (int q = 0; q <= QI; ++q) {
+        const int j = lane + 32 * q;
+        if (j < i) y[q] = fmaf(-A[j * ms + i], xi, y[q]);
+      }
+    }
+  }
+}
+__device__ void lu_solve_warp(const float* A, int m, int ms, const float* uinv, const float* b,
+                              float* x) {
+  const int lane = threadIdx.x & 31;
+  float y[7];
+#pragma unroll
+  for (int q = 0; q < 7; ++q) y[q] = (lane + 32 * q < m) ? b[lane + 32 * q] : 0.f;
+  lu_fwd_group<0>(A, m, ms, y, lane);
+  lu_fwd_group<1>(A, m, ms, y, lane);
+  lu_fwd_group<2>(A, m, ms, y, lane);
+  lu_fwd_group<3>(A, m, ms, y, lane);
+  lu_fwd_group<4>(A, m, ms, y, lane);
+  lu_fwd_group<5>(A, m, ms, y, lane);
+  lu_fwd_group<6>(A, m, ms, y, lane);
+  lu_bwd_group<6>(A, m, ms, uinv, y, lane);
+  lu_bwd_group<5>(A, m, ms, uinv, y, lane);
+  lu_bwd_group<4>(A, m, ms, uinv, y, lane);
+  lu_bwd_group<3>(A, m, ms, uinv, y, lane);
+  lu_bwd_group<2>(A, m, ms, uinv, y, lane);
+  lu_bwd_group<1>(A, m, ms, uinv, y, lane);
+  lu_bwd_group<0>(A, m, ms, uinv, y, lane);
+#pragma unroll
+  for (int q = 0; q < 7; ++q)
+    if (lane + 32 * q < m) x[lane + 32 * q] = y[q];
+  __syncwarp();
+}
+
+// ---------------------------------------------------------------------------------------
+// Compact single-warp factorizations of a 32 x 32 diagonal block.  Lane r keeps the not yet
+// final part of row r in registers, shifted so that a[0] is always the current column: one
+// step is a rank-1 update fused with the shift a[t] <- a[t + 1] - f b[t], b the broadcast
+// column (or row) in shared memory read with 16-byte loads.  The step loop stays rolled (the
+// kernels run once per launch on one SM, where code size costs more than loop overhead) and
+// every register index is a constant.
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ void shift_update(float (&a)[32], float f, const float* b) {
+#pragma unroll
+  for (int t4 = 0; t4 < 8; ++t4) {
+    const float4 v = reinterpret_cast<const float4*>(b)[t4];
+    a[4 * t4 + 0] = fmaf(-f, v.x, a[4 * t4 + 1]);
+    a[4 * t4 + 1] = fmaf(-f, v.y, a[4 * t4 + 2]);
+    a[4 * t4 + 2] = fmaf(-f, v.z, a[4 * t4 + 3]);
+    a[4 * t4 + 3] = (t4 < 7) ? fmaf(-f, v.w, a[4 * t4 + 4]) : 0.f;
+  }
+}
+
+// Cholesky of the kb x kb diagonal block at (k0, k0), kb <= 32, by one warp.  buf: 128 floats,
+// 16-byte aligned (two halves: the column below the pivot at [0, 32), the pivot at [32]).
+// On return the block holds L (lower, diagonal included) and dinv[0..kb) = 1 / L_cc.
+__device__ void chol_diag_rot(float* A, int ms, int k0, int kb, float* dinv, float* buf, int* bad) {
+  const int lane = threadIdx.x & 31;
+  const bool live = lane < kb;
+  float* row = A + (size_t)(k0 + (live ? lane : 0)) * ms + k0;
+  float a[32];
+#pragma unroll
+  for (int c = 0; c < 32; ++c) {
+    float v = (c == lane) ? 1.f : 0.f;
+    if (live && c <= lane) v = row[c];
+    a[c] = v;
+  }
+  float dmine = 1.f;
+  for (int kk = 0; kk < kb; ++kk) {
+    float* b = buf + 64 * (kk & 1);
+    if (lane > kk) b[lane - kk - 1] = a[0];  // a_lane,kk below the pivot
+    else if (lane == kk) b[32] = a[0];       // pivot
     __syncwarp();
+    float d = b[32];
+    if (lane == kk) dmine = d;
+    if (!(d > 0.f)) d = 1e-30f;
+    const float f = __fdividef(a[0], d);
+    if (live && lane > kk) row[kk] = a[0];   // unscaled L entry (l_rk d_k)
+    shift_update(a, f, b);
   }
-  float di = 1.f;
-  if (lane < kb) {
-    float piv = T[lane * ms + lane];
-    if (!(piv > 0.f)) { *bad = 1; piv = 1e-30f; }
-    di = rsqrtf(piv);
-    dinv[lane] = di;
+  if (live && !(dmine > 0.f)) { *bad = 1; dmine = 1e-30f; }
+  const float di = rsqrtf(dmine);
+  __syncwarp();
+  if (live) dinv[lane] = di;
+  __syncwarp();
+  if (live) {
+    for (int c = 0; c < lane; ++c) row[c] *= dinv[c];
+    row[lane] = 1.f / di;
   }
   __syncwarp();
-  if (lane < kb) {
-    for (int c = 0; c < lane; ++c) T[lane * ms + c] *= dinv[c];
-    T[lane * ms + lane] = 1.f / di;
+}
+
+// LU without pivoting of the kb x kb diagonal block at (k0, k0) by one warp: unit-lower
+// multipliers below the diagonal, U on and above it; uinv[k0 + c] = 1 / U_cc.  Row kk is
+// broadcast from lane kk by shuffles (one per register of the shifted row).  Also writes the
+// shifted copies used by the panel solves: Ush[c][t] = U_c,c+1+t and Lsh[c][t] = L_c+1+t,c
+// (32 x 32 each, zero outside the block).  A pivot below 1e-3 |dref| sets *unstable.
+__device__ void lu_diag_rot(float* A, int ms, int k0, int kb, float* buf, const float* dref,
+                            float* uinv, float* Ush, float* Lsh, int* unstable) {
+  (void)buf;
+  const int lane = threadIdx.x & 31;
+  const bool live = lane < kb;
+  float* row = A + (size_t)(k0 + (live ? lane : 0)) * ms + k0;
+  float a[32];
+#pragma unroll
+  for (int c = 0; c < 32; ++c) {
+    float v = (c == lane) ? 1.f : 0.f;
+    if (live) v = (c < kb) ? row[c] : 0.f;
+    a[c] = v;
+  }
+#pragma unroll
+  for (int t = 0; t < 32; ++t) { Ush[lane * 32 + t] = 0.f; Lsh[lane * 32 + t] = 0.f; }
+  __syncwarp();
+  for (int kk = 0; kk < kb; ++kk) {
+    float u = __shfl_sync(0xffffffff, a[0], kk);
+    if (!(fabsf(u) >= 1e-3f * dref[k0 + kk])) {
+      if (lane == 0) *unstable = 1;
+      if (u == 0.f) u = 1e-30f;
+    }
+    const bool below = lane > kk;
+    const float f = __fdividef(a[0], u);
+    if (below && live) {
+      row[kk] = f;
+      Lsh[kk * 32 + lane - kk - 1] = f;
+    }
+#pragma unroll
+    for (int t = 0; t < 32; ++t) {
+      const float nxt = t < 31 ? a[t + 1] : 0.f;
+      const float v = __shfl_sync(0xffffffff, nxt, kk);
+      if (below) a[t] = fmaf(-f, v, nxt);
+    }
+  }
+  // lane r stopped shifting at step r: a[t] = U_r,r+t
+  if (live) {
+#pragma unroll
+    for (int t = 0; t < 32; ++t) {
+      if (t < kb - lane) {
+        row[lane + t] = a[t];
+        if (t > 0) Ush[lane * 32 + t - 1] = a[t];
+      }
+    }
+    uinv[k0 + lane] = 1.f / (a[0] == 0.f ? 1e-30f : a[0]);
   }
   __syncwarp();
+}
+
+// x = a U^{-1} for one row a (kb entries at ar), U the block whose shifted rows are in Ush and
+// whose reciprocal diagonal is ui (right-looking, shifted registers)
+__device__ __forceinline__ void trsm_row_rot(float* ar, int kb, const float* Ush, const float* ui) {
+  float a[32];
+#pragma unroll
+  for (int c = 0; c < 32; ++c) a[c] = c < kb ? ar[c] : 0.f;
+  for (int c = 0; c < kb; ++c) {
+    const float x = a[0] * ui[c];
+    ar[c] = x;
+    shift_update(a, x, Ush + c * 32);
+  }
+}
+
+// y = L^{-1} a for one column a (kb entries, stride ms, at ac), L unit lower with shifted
+// columns in Lsh
+__device__ __forceinline__ void trsm_col_rot(float* ac, int ms, int kb, const float* Lsh) {
+  float a[32];
+#pragma unroll
+  for (int r = 0; r < 32; ++r) a[r] = r < kb ? ac[r * ms] : 0.f;
+  for (int r = 0; r < kb; ++r) {
+    const float y = a[0];
+    ac[r * ms] = y;
+    shift_update(a, y, Lsh + r * 32);
+  }
 }
 
 // Cholesky of the kb x kb diagonal block at (k0, k0) by the whole CTA in shared memory.  Step
@@ -316,27 +536,39 @@ __device__ void fwd_lower_warp(const float* A, int m, int ms, const float* b, fl
 }
 
 // one warp: L^T x = z with the reciprocals of diag(L) given; lane t keeps x[t + 32 q] in
-// registers (m <= 224), the newly final x_i is broadcast by shuffle
+// registers (m <= 224), the newly final x_i is broadcast by shuffle; the register group of x_i
+// is a compile-time index
+template <int QI>
+__device__ __forceinline__ void ltsolve_group(const float* __restrict__ A, int m, int ms,
+                                              const float* __restrict__ dinv, float (&xr)[7],
+                                              int lane) {
+  if (32 * QI < m) {
+    for (int li = min(31, m - 1 - 32 * QI); li >= 0; --li) {
+      const int i = 32 * QI + li;
+      const float xi = __shfl_sync(0xffffffff, xr[QI], li) * dinv[i];
+      if (lane == li) xr[QI] = xi;
+      const float* ai = A + i * ms;
+#pragma unroll
+      for (int q = 0; q <= QI; ++q) {
+        const int j = lane + 32 * q;
+        if (j < i) xr[q] = fmaf(-ai[j], xi, xr[q]);
+      }
+    }
+  }
+}
 __device__ void bwd_lowerT_warp_reg(const float* __restrict__ A, int m, int ms,
                                     const float* __restrict__ dinv, const float* z, float* x) {
   const int lane = threadIdx.x & 31;
   float xr[7];
 #pragma unroll
   for (int q = 0; q < 7; ++q) xr[q] = (lane + 32 * q < m) ? z[lane + 32 * q] : 0.f;
-  for (int i = m - 1; i >= 0; --i) {
-    const int qi = i >> 5, li = i & 31;
-    float own = 0.f;
-#pragma unroll
-    for (int q = 0; q < 7; ++q) own = (q == qi) ? xr[q] : own;
-    const float xi = __shfl_sync(0xffffffff, own, li) * dinv[i];
-    const float* ai = A + i * ms;
-#pragma unroll
-    for (int q = 0; q < 7; ++q) {
-      const int j = lane + 32 * q;
-      if (j < i) xr[q] = fmaf(-ai[j], xi, xr[q]);
-      else if (j == i) xr[q] = xi;
-    }
-  }
+  ltsolve_group<6>(A, m, ms, dinv, xr, lane);
+  ltsolve_group<5>(A, m, ms, dinv, xr, lane);
+  ltsolve_group<4>(A, m, ms, dinv, xr, lane);
+  ltsolve_group<3>(A, m, ms, dinv, xr, lane);
+  ltsolve_group<2>(A, m, ms, dinv, xr, lane);
+  ltsolve_group<1>(A, m, ms, dinv, xr, lane);
+  ltsolve_group<0>(A, m, ms, dinv, xr, lane);
 #pragma unroll
   for (int q = 0; q < 7; ++q)
     if (lane + 32 * q < m) x[lane + 32 * q] = xr[q];
@@ -357,11 +589,11 @@ __device__ void bwd_lowerT_warp(const float* A, int m, int ms, const float* z, f
   }
 }
 
-__device__ void load_shifted_gram(float* A, int m, int ms, const double* G, int ldg, float mu) {
+__device__ void load_shifted_gram(float* A, int m, int ms, const float* G, int ldg, float mu) {
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5, nty = blockDim.x >> 5;
   for (int i = ty; i < m; i += nty)
     for (int j = tx; j <= i; j += 32)
-      A[i * ms + j] = (float)G[(int64_t)i * ldg + j] + (i == j ? mu : 0.f);
+      A[i * ms + j] = G[(int64_t)i * ldg + j] + (i == j ? mu : 0.f);
 }
 
 // f_k = || Q_s^{(m)} alpha_k - u_k ||^2 over the seeds: a warp per seed row (lanes over the
@@ -420,6 +652,76 @@ __device__ void seed_residuals(const float* __restrict__ Qs, int ldq, const floa
 }
 
 // ---------------------------------------------------------------------------------------
+// [K | G | h | b] = Q_s^T [X | Q_s | r0 | U-hat_s] in FP32.  64 x 64 output tiles; the S seed
+// rows are split over the CTAs of a thread-block cluster along z.  Each CTA keeps its partial
+// tile in shared memory, and the rank-0 CTA of the cluster adds the partials in rank order
+// through distributed shared memory, so the sums have a fixed order.  (S is a few thousand at
+// most, so FP32 partial sums over S / cluster rows are accurate to a few ulps of the result.)
+// ---------------------------------------------------------------------------------------
+constexpr int kSgT = 64, kSgK = 32, kSgMaxCluster = 8;
+
+__global__ void __launch_bounds__(256)
+k_seed_gram(const float* __restrict__ A, int lda, const float* __restrict__ B, int ldb, int S,
+            int p, int q, float* __restrict__ Gout, int ldg) {
+  rw_grid_wait();
+  rw_grid_trigger();
+  cg::cluster_group cluster = cg::this_cluster();
+  __shared__ float As[kSgK][kSgT + 4];
+  __shared__ float Bs[kSgK][kSgT + 4];
+  __shared__ float4 part[kSgT * kSgT / 4];
+  const int i0 = blockIdx.x * kSgT, j0 = blockIdx.y * kSgT;
+  const int nz = gridDim.z, rank = (int)cluster.block_rank();
+  const int rpc = ((S + nz - 1) / nz + kSgK - 1) / kSgK * kSgK;
+  const int r0 = rank * rpc, r1 = min(S, r0 + rpc);
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  float acc[4][4] = {};
+  for (int k0 = r0; k0 < r1; k0 += kSgK) {
+    for (int e = threadIdx.x; e < kSgK * kSgT; e += 256) {
+      const int kk = e / kSgT, ii = e % kSgT;
+      const int r = k0 + kk;
+      const bool rin = r < r1;
+      As[kk][ii] = (rin && i0 + ii < p) ? A[(int64_t)r * lda + i0 + ii] : 0.f;
+      Bs[kk][ii] = (rin && j0 + ii < q) ? B[(int64_t)r * ldb + j0 + ii] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int kk = 0; kk < kSgK; ++kk) {
+      float a[4], b[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) { a[u] = As[kk][ty * 4 + u]; b[u] = Bs[kk][tx * 4 + u]; }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(a[u], b[v], acc[u][v]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+    part[(ty * 4 + u) * 16 + tx] = make_float4(acc[u][0], acc[u][1], acc[u][2], acc[u][3]);
+  cluster.sync();
+  if (rank == 0) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      float4 sum = part[(ty * 4 + u) * 16 + tx];
+      for (int r = 1; r < nz; ++r) {
+        const float4 o = cluster.map_shared_rank(part, r)[(ty * 4 + u) * 16 + tx];
+        sum.x += o.x; sum.y += o.y; sum.z += o.z; sum.w += o.w;
+      }
+      const int i = i0 + ty * 4 + u;
+      const float vals[4] = {sum.x, sum.y, sum.z, sum.w};
+      if (i < p)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          const int j = j0 + tx * 4 + v;
+          if (j < q) Gout[(int64_t)i * ldg + j] = vals[v];
+        }
+    }
+  }
+  cluster.sync();  // the peers' partial tiles stay alive until rank 0 has read them
+}
+
+// ---------------------------------------------------------------------------------------
 // Adaptive m (Sec. III-A-1, Eq. alpha_1) in one CTA of 256 threads:
 //   f_k(m) = min_{||a|| <= rho} || Q_s^{(m)} a - u_k ||^2,  candidates m = m_step, 2 m_step, ...
 // The candidates are nested, so the Cholesky factor of G + mu0 I (G = Q_s^T Q_s, mu0 = 1e-6
@@ -433,10 +735,12 @@ __device__ void seed_residuals(const float* __restrict__ Qs, int ldq, const floa
 // ---------------------------------------------------------------------------------------
 template <int LP>
 __global__ void __launch_bounds__(256, 1)
-k_adapt(const double* __restrict__ G, int ldg, const double* __restrict__ bv, int ldb,
+k_adapt(const float* __restrict__ G, int ldg, const float* __restrict__ bv, int ldb,
         const float* __restrict__ Qs, int ldq, const float* __restrict__ Us, int ldu, int S,
         int L, int mmax, int mstep, double rho, double fmax, int* __restrict__ mdev,
         double* __restrict__ fsel) {
+  rw_grid_wait();
+  rw_grid_trigger();
   extern __shared__ float sm[];
   const int ms = mmax | 1;
   float* A = sm;                          // mmax x ms, lower factor
@@ -445,6 +749,7 @@ k_adapt(const double* __restrict__ G, int ldg, const double* __restrict__ bv, in
   float* al = bb + (size_t)L * mmax;      // L x mmax
   __shared__ float ck[RW_MAX_LABELS], zz[RW_MAX_LABELS], fk[RW_MAX_LABELS], nk[RW_MAX_LABELS];
   __shared__ float dinv[kMaxSmallM];  // reciprocals of diag(L)
+  __shared__ __align__(16) float colbuf[128];
   __shared__ float mu0s, red;
   __shared__ int chosen, bad, done, capped;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
@@ -454,10 +759,13 @@ k_adapt(const double* __restrict__ G, int ldg, const double* __restrict__ bv, in
   if (tid < RW_MAX_LABELS) { ck[tid] = 0.f; zz[tid] = 0.f; }
   if (tid == 0) { chosen = -1; bad = 0; done = 0; capped = 0; }
   __syncthreads();
+  if (tid == 0) red = 0.f;
+  __syncthreads();
   {
     float acc[LP];
 #pragma unroll
     for (int k = 0; k < LP; ++k) acc[k] = 0.f;
+#pragma unroll 4
     for (int s = tid; s < S; s += blockDim.x)
 #pragma unroll
       for (int k = 0; k < LP; ++k)
@@ -467,17 +775,19 @@ k_adapt(const double* __restrict__ G, int ldg, const double* __restrict__ bv, in
       float v = warp_sum(acc[k]);
       if (lane == 0 && k < L) atomicAdd(&ck[k], v);
     }
+    // trace of G (for mu0): one diagonal entry per thread
+    float tr = 0.f;
+    for (int i = tid; i < mmax; i += blockDim.x) tr += G[(int64_t)i * ldg + i];
+    tr = warp_sum(tr);
+    if (lane == 0) atomicAdd(&red, tr);
   }
-  if (warp == 0) {
-    double tr = 0.0;
-    for (int i = lane; i < mmax; i += 32) tr += G[(int64_t)i * ldg + i];
-    for (int o = 16; o > 0; o >>= 1) tr += __shfl_xor_sync(0xffffffff, tr, o);
-    if (lane == 0) mu0s = (float)(1e-6 * tr / mmax);
-  }
+#pragma unroll 4
   for (int e = tid; e < L * mmax; e += blockDim.x) {
     const int k = e / mmax, i = e % mmax;
-    bb[e] = (float)bv[(int64_t)i * ldb + k];
+    bb[e] = bv[(int64_t)i * ldb + k];
   }
+  __syncthreads();
+  if (tid == 0) mu0s = 1e-6f * red / mmax;
   __syncthreads();
   const float mu0 = mu0s;
   int rows_done = 0;
@@ -486,7 +796,7 @@ k_adapt(const double* __restrict__ G, int ldg, const double* __restrict__ bv, in
     // tile row K of G + mu0 I (columns 0 .. r0 + nr)
     for (int i = r0 + warp; i < r0 + nr; i += nw)
       for (int j = lane; j <= i; j += 32)
-        A[i * ms + j] = (float)G[(int64_t)i * ldg + j] + (i == j ? mu0 : 0.f);
+        A[i * ms + j] = G[(int64_t)i * ldg + j] + (i == j ? mu0 : 0.f);
     __syncthreads();
     // off-diagonal tiles L_KJ = (A_KJ - sum_{t<J} L_Kt L_Jt^T) L_JJ^{-T}, J = 0..K-1 in order
     for (int J = 0; J < K; ++J) {
@@ -535,7 +845,7 @@ k_adapt(const double* __restrict__ G, int ldg, const double* __restrict__ bv, in
       }
     }
     __syncthreads();
-    if (warp == 0) chol_diag_block_warp(A, ms, r0, nr, dinv + r0, &bad);
+    if (warp == 0) chol_diag_rot(A, ms, r0, nr, dinv + r0, colbuf, &bad);
     __syncthreads();
     // z_k on tile K: z = L_KK^{-1} (b_K - sum_J L_KJ z_J), one warp per label
     for (int k = warp; k < L; k += nw) {
@@ -619,7 +929,7 @@ k_adapt(const double* __restrict__ G, int ldg, const double* __restrict__ bv, in
       __syncthreads();
       bool okc = chol_lower_smem(B2, m, mss);
       for (int k = warp; k < L; k += nw) {
-        for (int i = lane; i < m; i += 32) z[k * mmax + i] = (float)bv[(int64_t)i * ldb + k];
+        for (int i = lane; i < m; i += 32) z[k * mmax + i] = bv[(int64_t)i * ldb + k];
         __syncwarp();
         fwd_lower_warp(B2, m, mss, z + k * mmax, z + k * mmax);
         bwd_lowerT_warp(B2, m, mss, z + k * mmax, al + k * mmax);
@@ -649,7 +959,7 @@ k_adapt(const double* __restrict__ G, int ldg, const double* __restrict__ bv, in
           __syncthreads();
           if (!chol_lower_smem(B2, m, mss)) { okc = false; break; }
           if (warp == 0) {
-            for (int i = lane; i < m; i += 32) z[k * mmax + i] = (float)bv[(int64_t)i * ldb + k];
+            for (int i = lane; i < m; i += 32) z[k * mmax + i] = bv[(int64_t)i * ldb + k];
             __syncwarp();
             fwd_lower_warp(B2, m, mss, z + k * mmax, z + k * mmax);
             bwd_lowerT_warp(B2, m, mss, z + k * mmax, al + k * mmax);
@@ -679,6 +989,8 @@ k_adapt(const double* __restrict__ G, int ldg, const double* __restrict__ bv, in
 }
 
 __global__ void k_set_m(int* mdev, int m) {
+  rw_grid_wait();
+  rw_grid_trigger();
   if (threadIdx.x == 0) { mdev[0] = m; mdev[1] = 0; }
 }
 
@@ -722,6 +1034,8 @@ __global__ void __launch_bounds__(256)
 k_project(const T* __restrict__ Q, int ldq, int cpr, const float* __restrict__ phat,
           const int* __restrict__ seedlab, int64_t N, const int* __restrict__ mdev,
           float* __restrict__ part) {
+  rw_grid_wait();
+  rw_grid_trigger();
   constexpr int V = Vec16<T>::V;
   constexpr int U = 4;  // rows per warp iteration
   extern __shared__ float zacc[];  // ldq * LP
@@ -795,14 +1109,21 @@ k_project(const T* __restrict__ Q, int ldq, int cpr, const float* __restrict__ p
 
 // Z (mq x lp, FP64) = scale * sum over blocks of the partials; one warp per entry, fixed order
 __global__ void k_reduce_partials(const float* __restrict__ part, int nblk, int ldq, int lp,
-                                  int mq, double scale, double* __restrict__ Z) {
+                                  int mq, float scale, float* __restrict__ Z,
+                                  const double* __restrict__ lam, double gamma, int m,
+                                  float* __restrict__ lgam) {
+  rw_grid_wait();
+  rw_grid_trigger();
+  // one warp per entry of Z: lane l adds the partials l, l + 32, ... in order, then a fixed
+  // butterfly; also lgam = lambda + gamma in FP32 for the small system
   const int lane = threadIdx.x & 31;
   const int e = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (e < m && lane == 0) lgam[e] = (float)(lam[e] + gamma);
   if (e >= mq * lp) return;
   const int row = e / lp;
-  double s = 0.0;
+  float s = 0.f;
   if (row < ldq)
-    for (int b = lane; b < nblk; b += 32) s += (double)part[(int64_t)b * ldq * lp + e];
+    for (int b = lane; b < nblk; b += 32) s += part[(int64_t)b * ldq * lp + e];
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffff, s, o);
   if (lane == 0) Z[e] = s * scale;
@@ -812,98 +1133,107 @@ __global__ void k_reduce_partials(const float* __restrict__ part, int nblk, int 
 // Small system of Eq. (Fs) in Woodbury form, one CTA:
 //   M = diag(lambda + gamma) - K_m,  M y = h + gamma K (Lambda_gamma Z),  C = y + gamma Lambda_gamma Z
 // LU in FP32 shared memory.  M is diagonally dominant in practice (its off-diagonal part is
-// Q_s^T X, small next to lambda + gamma), so the elimination first runs without pivoting (one
-// barrier per step, multipliers left unscaled: l_ik = a_ik / u_kk applied on the fly).  If a
-// pivot falls below 1e-3 of its original diagonal entry, M is reloaded and eliminated with
-// partial pivoting (rows permuted through an index array, two barriers per step).
+// Q_s^T X, small next to lambda + gamma), so the elimination first runs without pivoting,
+// blocked by 32-column panels.  If a pivot falls below 1e-3 of its original diagonal entry, M
+// is reloaded and eliminated with partial pivoting (rows permuted through an index array).
 // ---------------------------------------------------------------------------------------
-__device__ void load_M(float* M, int m, int ms, const double* __restrict__ K, int ldk,
-                       const double* __restrict__ lam, double gamma) {
-  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5, nty = blockDim.x >> 5;
-  for (int i = ty; i < m; i += nty)
-    for (int j = tx; j < m; j += 32) {
-      float v = -(float)K[(int64_t)i * ldk + j];
-      if (i == j) v += (float)(lam[i] + gamma);
-      M[i * ms + j] = v;
+__device__ void load_M(float* M, int m, int ms, const float* __restrict__ K, int ldk,
+                       const float* __restrict__ lgam) {
+  // M = diag(lambda + gamma) - K: a warp per row, the row's loads (m <= 224: at most 7 per
+  // lane) issued together
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int i = warp; i < m; i += nw) {
+    const float* kr = K + (int64_t)i * ldk;
+    float v[7];
+#pragma unroll
+    for (int q = 0; q < 7; ++q) {
+      const int j = lane + 32 * q;
+      v[q] = j < m ? kr[j] : 0.f;
     }
+#pragma unroll
+    for (int q = 0; q < 7; ++q) {
+      const int j = lane + 32 * q;
+      if (j < m) M[i * ms + j] = (j == i ? lgam[i] : 0.f) - v[q];
+    }
+  }
 }
 
 template <int LP>
 __global__ void __launch_bounds__(256, 1)
-k_small_solve(const double* __restrict__ K, int ldk, const double* __restrict__ h, int ldh,
-              const double* __restrict__ Z, const double* __restrict__ lam, double gamma,
+k_small_solve(const float* __restrict__ K, int ldk, const float* __restrict__ h, int ldh,
+              const float* __restrict__ Z, const float* __restrict__ lgam, float gamma,
               int L, int lp, int mq, const int* __restrict__ mdev, float* __restrict__ C,
               int* status) {
+  rw_grid_wait();
+  rw_grid_trigger();
   extern __shared__ float sm[];
   const int m = mdev[0];
   const int ms = m | 1;
   float* M = sm;                       // m x ms
-  float* W = M + (size_t)m * ms;       // m x L : Lambda_gamma Z
-  float* B = W + (size_t)m * L;        // m x L : right-hand sides
-  float* Y = B + (size_t)m * L;        // m x L : solution
+  float* W = M + (size_t)m * ms;       // m x L : Lambda_gamma Z (row-major)
+  float* B = W + (size_t)m * L;        // L x m : right-hand sides (label-major)
+  float* Y = B + (size_t)m * L;        // L x m : solution (label-major)
   int* perm = reinterpret_cast<int*>(Y + (size_t)m * L);  // m
-  float* invd = reinterpret_cast<float*>(perm + m);       // m
+  float* dref = reinterpret_cast<float*>(perm + m);       // m : |M_ii| before elimination
+  __shared__ float uinv[kMaxSmallM];
+  __shared__ __align__(16) float buf[128];
+  __shared__ __align__(16) float Ush[32 * 32], Lsh[32 * 32];
   __shared__ int bad, unstable;
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5, nty = blockDim.x >> 5;
   const int warp = ty, lane = tx;
   if (threadIdx.x == 0) { bad = 0; unstable = 0; }
   for (int e = threadIdx.x; e < m * L; e += blockDim.x) {
-    int i = e / L, k = e % L;
-    W[i * L + k] = (float)(Z[(int64_t)i * lp + k] / (lam[i] + gamma));
+    const int i = e / L, k = e % L;
+    W[i * L + k] = __fdividef(Z[(int64_t)i * lp + k], lgam[i]);
+    B[k * m + i] = h[(int64_t)i * ldh + k];
   }
-  load_M(M, m, ms, K, ldk, lam, gamma);
+  load_M(M, m, ms, K, ldk, lgam);
+  __syncthreads();
   for (int i = threadIdx.x; i < m; i += blockDim.x) {
     perm[i] = i;
-    invd[i] = fabsf((float)(lam[i] + gamma) - (float)K[(int64_t)i * ldk + i]);  // |M_ii|
+    dref[i] = fabsf(M[i * ms + i]);  // |M_ii| before elimination
   }
   __syncthreads();
-  // B = h + gamma K W, with K read back from the shared copy of M (K_ij = -M_ij off the
-  // diagonal, K_ii = lambda_i + gamma - M_ii): a warp per row, lanes over the columns
-  for (int i = warp; i < m; i += nty) {
-    float acc[LP];
-#pragma unroll
-    for (int k = 0; k < LP; ++k) acc[k] = 0.f;
-    const float dii = (float)(lam[i] + gamma);
-    for (int j = lane; j < m; j += 32) {
-      const float kij = (j == i) ? dii - M[i * ms + j] : -M[i * ms + j];
-#pragma unroll
-      for (int k = 0; k < LP; ++k)
-        if (k < L) acc[k] = fmaf(kij, W[j * L + k], acc[k]);
+  // B += gamma K W, with K read back from the shared copy of M (K_ij = -M_ij off the diagonal,
+  // K_ii = lambda_i + gamma - M_ii): one thread per (row, label), the row walked in order
+  for (int e = threadIdx.x; e < m * L; e += blockDim.x) {
+    const int i = e % m, k = e / m;
+    const float* mi = M + (size_t)i * ms;
+    float acc0 = 0.f, acc1 = 0.f;
+    int j = 0;
+    for (; j + 1 < m; j += 2) {
+      acc0 = fmaf(-mi[j], W[j * L + k], acc0);
+      acc1 = fmaf(-mi[j + 1], W[(j + 1) * L + k], acc1);
     }
-#pragma unroll
-    for (int k = 0; k < LP; ++k) {
-      const float sk = warp_sum(acc[k]);
-      if (lane == 0 && k < L) B[i * L + k] = (float)h[(int64_t)i * ldh + k] + (float)gamma * sk;
-    }
+    if (j < m) acc0 = fmaf(-mi[j], W[j * L + k], acc0);
+    const float kii_extra = lgam[i] * W[i * L + k];   // diagonal: K_ii = lgam_i - M_ii
+    B[k * m + i] += gamma * (acc0 + acc1 + kii_extra);
   }
-  // elimination without pivoting
-  for (int k = 0; k < m; ++k) {
-    float pv = M[k * ms + k];
-    if (!(fabsf(pv) >= 1e-3f * invd[k])) {
-      if (threadIdx.x == 0) unstable = 1;
-      pv = (pv == 0.f) ? 1e-30f : pv;
-    }
-    const float inv = 1.f / pv;
-    float rowk[8];
-#pragma unroll
-    for (int c = 0; c < 8; ++c) {
-      const int j = k + 1 + tx + 32 * c;
-      rowk[c] = (j < m) ? M[k * ms + j] : 0.f;
-    }
-    for (int i = k + 1 + ty; i < m; i += nty) {
-      const float a = M[i * ms + k] * inv;
-#pragma unroll
-      for (int c = 0; c < 8; ++c) {
-        const int j = k + 1 + tx + 32 * c;
-        if (j < m) M[i * ms + j] = fmaf(-a, rowk[c], M[i * ms + j]);
+  __syncthreads();
+  // blocked LU without pivoting, 32-column panels: the diagonal block on one warp in
+  // registers, the two triangular solves one row / column per thread, the trailing update in
+  // 4 x 4 register tiles
+  for (int p0 = 0; p0 < m; p0 += 32) {
+    const int kb = min(32, m - p0);
+    if (warp == 0) lu_diag_rot(M, ms, p0, kb, buf, dref, uinv, Ush, Lsh, &unstable);
+    __syncthreads();
+    const int r1 = p0 + kb, n = m - r1;
+    if (n > 0) {
+      for (int t = threadIdx.x; t < 2 * n; t += blockDim.x) {
+        if (t < n) trsm_row_rot(M + (size_t)(r1 + t) * ms + p0, kb, Ush, uinv + p0);
+        else trsm_col_rot(M + (size_t)p0 * ms + r1 + (t - n), ms, kb, Lsh);
       }
+      __syncthreads();
+      gemm_trailing(M, ms, m, r1, p0, kb);
+      __syncthreads();
     }
-    __syncthreads();
   }
-  if (unstable) {
-    // partial pivoting from the original M
+  if (!unstable) {
+    for (int k = warp; k < L; k += nty) lu_solve_warp(M, m, ms, uinv, B + (size_t)k * m, Y + (size_t)k * m);
+  } else {
+    // a pivot fell below 1e-3 of its original diagonal: partial pivoting from the original M
     __syncthreads();
-    load_M(M, m, ms, K, ldk, lam, gamma);
+    load_M(M, m, ms, K, ldk, lgam);
     for (int k = 0; k < m; ++k) {
       __syncthreads();
       if (warp == 0) {  // pivot among the rows perm[k..m-1]
@@ -935,32 +1265,33 @@ k_small_solve(const double* __restrict__ K, int ldk, const double* __restrict__ 
       }
     }
     __syncthreads();
-  }
-  for (int i = threadIdx.x; i < m; i += blockDim.x) invd[i] = 1.f / M[perm[i] * ms + i];
-  __syncthreads();
-  // forward (unit lower, multipliers a_ij / u_jj) and backward (upper) substitution, column
-  // oriented, one warp per label
-  for (int k = warp; k < L; k += nty) {
-    for (int i = lane; i < m; i += 32) Y[i * L + k] = B[perm[i] * L + k];
-    __syncwarp();
-    for (int j = 0; j < m; ++j) {
-      const float f = Y[j * L + k] * invd[j];
-      for (int i = j + 1 + lane; i < m; i += 32) Y[i * L + k] = fmaf(-M[perm[i] * ms + j], f, Y[i * L + k]);
+    for (int i = threadIdx.x; i < m; i += blockDim.x) uinv[i] = 1.f / M[perm[i] * ms + i];
+    __syncthreads();
+    // forward (unit lower, multipliers a_ij / u_jj) and backward (upper) substitution on the
+    // permuted rows, one warp per label
+    for (int k = warp; k < L; k += nty) {
+      float* y = Y + (size_t)k * m;
+      for (int i = lane; i < m; i += 32) y[i] = B[(size_t)k * m + perm[i]];
       __syncwarp();
-    }
-    for (int i = m - 1; i >= 0; --i) {
-      const float yi = Y[i * L + k] * invd[i];
-      __syncwarp();
-      if (lane == 0) Y[i * L + k] = yi;
-      for (int j = lane; j < i; j += 32) Y[j * L + k] = fmaf(-M[perm[j] * ms + i], yi, Y[j * L + k]);
-      __syncwarp();
+      for (int j = 0; j < m; ++j) {
+        const float f = y[j] * uinv[j];
+        for (int i = j + 1 + lane; i < m; i += 32) y[i] = fmaf(-M[perm[i] * ms + j], f, y[i]);
+        __syncwarp();
+      }
+      for (int i = m - 1; i >= 0; --i) {
+        const float yi = y[i] * uinv[i];
+        __syncwarp();
+        if (lane == 0) y[i] = yi;
+        for (int j = lane; j < i; j += 32) y[j] = fmaf(-M[perm[j] * ms + i], yi, y[j]);
+        __syncwarp();
+      }
     }
   }
   __syncthreads();
   for (int e = threadIdx.x; e < mq * lp; e += blockDim.x) {
     int i = e / lp, k = e % lp;
     float v = 0.f;
-    if (i < m && k < L) v = Y[i * L + k] + (float)gamma * W[i * L + k];
+    if (i < m && k < L) v = Y[(size_t)k * m + i] + gamma * W[i * L + k];
     C[e] = v;
   }
   if (threadIdx.x == 0 && bad) atomicOr(status, RW_DEV_SINGULAR);
@@ -980,6 +1311,8 @@ k_backproject(const T* __restrict__ Q, int ldq, int cpr, const float* __restrict
               float cscale, const int* __restrict__ seedlab, const float* __restrict__ sq,
               const float* __restrict__ s, int64_t N, int L, const int* __restrict__ mdev,
               float* __restrict__ xhat, float* __restrict__ U, uint8_t* __restrict__ labels) {
+  rw_grid_wait();
+  rw_grid_trigger();
   constexpr int V = Vec16<T>::V;
   constexpr int RB = 16 / LP;  // rows per warp iteration
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -1080,6 +1413,8 @@ __global__ void __launch_bounds__(256)
 k_project_panel(const T* __restrict__ Qp, int64_t N, int nchunk_max,
                 const float* __restrict__ phat, const int* __restrict__ seedlab,
                 const int* __restrict__ mdev, float* __restrict__ part) {
+  rw_grid_wait();
+  rw_grid_trigger();
   constexpr int NV = 8 * LP;       // products per row and chunk
   constexpr int NG = NV / 32;      // groups of 32 reduced at once
   extern __shared__ float red[];   // nw x (nchunk_max * NV)
@@ -1154,6 +1489,8 @@ k_backproject_panel(const T* __restrict__ Qp, int64_t N, int nchunk_max,
                     const float* __restrict__ sq, const float* __restrict__ s, int L,
                     const int* __restrict__ mdev, float* __restrict__ xhat,
                     float* __restrict__ U, uint8_t* __restrict__ labels) {
+  rw_grid_wait();
+  rw_grid_trigger();
   extern __shared__ float Cs[];  // (8 nchunk_max) x LP
   const int m = mdev[0];
   const int nch = min((m + 7) / 8, nchunk_max);
@@ -1232,6 +1569,8 @@ k_jacobi_step(const float* __restrict__ xin, float* __restrict__ xout,
               int DZ, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colv,
               const float* __restrict__ ccsr, int64_t N, int L, float gamma, float omega,
               int last, float* __restrict__ U, uint8_t* __restrict__ labels) {
+  rw_grid_wait();
+  rw_grid_trigger();
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
   constexpr int NV = LP / 4;
@@ -1300,11 +1639,10 @@ template <int LP>
 rw_status launch_jacobi(const rw_graph* g, const float* xin, float* xout, const float* phat,
                         const int* seedlab, int L, float gamma, float omega, int last,
                         float* U, uint8_t* labels, cudaStream_t st) {
-  k_jacobi_step<LP><<<rw_blocks(g->N, 256), 256, 0, st>>>(
+  RW_LAUNCH((k_jacobi_step<LP>), rw_blocks(g->N, 256), 256, 0, st, 
       xin, xout, phat, seedlab, g->cw, g->d, g->s, g->normalized, g->kind, g->ndim, g->dims[0],
       g->dims[1], g->dims[2], g->rowptr, g->col, g->ccsr, g->N, L, gamma, omega, last, U,
       labels);
-  RW_LAUNCH_CHECK();
   return RW_OK;
 }
 
@@ -1331,10 +1669,10 @@ rw_status launch_proj_back(bool back, const T* Q, int ldq, const float* phat,
       const size_t shm = sizeof(float) * 8 * (size_t)nchunk * 8 * LP;
       if (shm > 48 * 1024)
         cudaFuncSetAttribute(k_project_panel<T, LP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
-      k_project_panel<T, LP><<<nblk, 256, shm, st>>>(Q, g->N, nchunk, phat, seedlab, mdev, part);
+      RW_LAUNCH((k_project_panel<T, LP>), nblk, 256, shm, st, Q, g->N, nchunk, phat, seedlab, mdev, part);
     } else {
       const size_t shm = sizeof(float) * (size_t)nchunk * 8 * LP;
-      k_backproject_panel<T, LP><<<nblk, 256, shm, st>>>(Q, g->N, nchunk, C, cscale, seedlab,
+      RW_LAUNCH((k_backproject_panel<T, LP>), nblk, 256, shm, st, Q, g->N, nchunk, C, cscale, seedlab,
                                                         g->sq, g->s, L, mdev, xhat, U, labels);
     }
     RW_LAUNCH_CHECK();
@@ -1343,17 +1681,17 @@ rw_status launch_proj_back(bool back, const T* Q, int ldq, const float* phat,
   if (!back) {
     size_t shm = sizeof(float) * ldq * LP;
     if (cpr <= 32)
-      k_project<T, LP, 1><<<nblk, 256, shm, st>>>(Q, ldq, cpr, phat, seedlab, g->N, mdev, part);
+      RW_LAUNCH((k_project<T, LP, 1>), nblk, 256, shm, st, Q, ldq, cpr, phat, seedlab, g->N, mdev, part);
     else if (cpr <= 64)
-      k_project<T, LP, 2><<<nblk, 256, shm, st>>>(Q, ldq, cpr, phat, seedlab, g->N, mdev, part);
+      RW_LAUNCH((k_project<T, LP, 2>), nblk, 256, shm, st, Q, ldq, cpr, phat, seedlab, g->N, mdev, part);
     else
       return RW_ERR_UNSUPPORTED;
   } else {
     if (cpr <= 32)
-      k_backproject<T, LP, 1><<<nblk, 256, 0, st>>>(Q, ldq, cpr, C, cscale, seedlab, g->sq, g->s,
+      RW_LAUNCH((k_backproject<T, LP, 1>), nblk, 256, 0, st, Q, ldq, cpr, C, cscale, seedlab, g->sq, g->s,
                                                    g->N, L, mdev, xhat, U, labels);
     else if (cpr <= 64)
-      k_backproject<T, LP, 2><<<nblk, 256, 0, st>>>(Q, ldq, cpr, C, cscale, seedlab, g->sq, g->s,
+      RW_LAUNCH((k_backproject<T, LP, 2>), nblk, 256, 0, st, Q, ldq, cpr, C, cscale, seedlab, g->sq, g->s,
                                                    g->N, L, mdev, xhat, U, labels);
     else
       return RW_ERR_UNSUPPORTED;
@@ -1391,6 +1729,29 @@ rw_status rw_solve_priors_internal(const rw_graph* g, const int32_t* seed_idx,
                                    const float* priors, int lp, cudaStream_t st, float** phat_out,
                                    int** seedlab_out, double** fit64_out);
 
+// launches k_seed_gram with the seed rows split over a cluster of up to 8 CTAs along z
+static rw_status seed_gram(const float* A, int lda, const float* B, int ldb, int S, int p, int q,
+                           float* G, int ldg, cudaStream_t st) {
+  const int nz = std::max(1, std::min(kSgMaxCluster, (S + 191) / 192));
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((p + kSgT - 1) / kSgT, (q + kSgT - 1) / kSgT, nz);
+  cfg.blockDim = dim3(256, 1, 1);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[2];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = 1;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = nz;
+  attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[1].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 2;
+  RW_CHECK_CUDA(cudaLaunchKernelEx(&cfg, k_seed_gram, A, lda, B, ldb, S, p, q, G, ldg));
+  rw_count_launch();
+  return RW_OK;
+}
+
 // ---------------------------------------------------------------------------------------
 // Seed bookkeeping and priors, shared by the fast solve, the PCG solve and the gradients
 // ---------------------------------------------------------------------------------------
@@ -1409,17 +1770,12 @@ rw_status rw_solve_priors_internal(const rw_graph* g, const int32_t* seed_idx,
   float* fit = reinterpret_cast<float*>(stats + 48);
   double* fit64 = reinterpret_cast<double*>(fit + 48);
   int* seedlab = ws.seedlab.as<int>();
-  k_fill_i32<<<rw_blocks(g->N, 256), 256, 0, st>>>(seedlab, g->N, -1);
-  RW_LAUNCH_CHECK();
-  RW_CHECK_CUDA(cudaMemsetAsync(stats, 0, sizeof(double) * 48, st));
-  k_seed_scatter<<<rw_blocks(S, 256), 256, 0, st>>>(seed_idx, seed_lab, S, L, g->N, g->J ? g->J : nullptr,
+  RW_LAUNCH(k_seed_reset, rw_blocks(g->N, 256), 256, 0, st, seedlab, g->N, stats, 48);
+  RW_LAUNCH(k_seed_scatter, rw_blocks(S, 256), 256, 0, st, seed_idx, seed_lab, S, L, g->N, g->J ? g->J : nullptr,
                                                     seedlab, stats, g->status);
-  RW_LAUNCH_CHECK();
-  k_fit<<<1, 32, 0, st>>>(stats, L, prior_mode, fit, fit64, g->status);
-  RW_LAUNCH_CHECK();
-  k_priors<<<rw_blocks(g->N, 256), 256, 0, st>>>(g->J, g->sq, g->N, L, lp, prior_mode, fit, priors,
+  RW_LAUNCH(k_fit, 1, 32, 0, st, stats, L, prior_mode, fit, fit64, g->status);
+  RW_LAUNCH(k_priors, rw_blocks(g->N, 256), 256, 0, st, g->J, g->sq, g->N, L, lp, prior_mode, fit, priors,
                                                  ws.phat.as<float>(), g->status);
-  RW_LAUNCH_CHECK();
   *phat_out = ws.phat.as<float>();
   *seedlab_out = seedlab;
   if (fit64_out) *fit64_out = fit64;
@@ -1446,7 +1802,10 @@ static rw_status validate_solve(const rw_graph* g, const rw_basis* b, const int3
   const size_t shm_adapt = sizeof(float) * ((size_t)mmax * (mmax | 1) + 3 * (size_t)L * mmax);
   const size_t shm_small = sizeof(float) * ((size_t)mmax * (mmax | 1) + 3 * (size_t)L * mmax + mmax) +
                            sizeof(int) * mmax;
-  if (std::max(o->m == 0 ? shm_adapt : 0, shm_small) > 227 * 1024) return RW_ERR_UNSUPPORTED;
+  // + the kernels' static shared arrays (reciprocal diagonals, broadcast buffers, the
+  // shifted copies of the LU panel's diagonal block)
+  constexpr size_t kStaticShm = 12 * 1024;
+  if (std::max(o->m == 0 ? shm_adapt : 0, shm_small) + kStaticShm > 227 * 1024) return RW_ERR_UNSUPPORTED;
   return RW_OK;
 }
 
@@ -1503,19 +1862,18 @@ extern "C" rw_status rw_solve(const rw_graph* g, const rw_basis* b, const int32_
   RW_TRY(mark(1));
   const int wcat = 2 * mp + 2 * lp;
   float* Bcat = reinterpret_cast<float*>(P(lay.Bcat));
-  double* Gcat = reinterpret_cast<double*>(P(lay.Gcat));
+  float* Gcat = reinterpret_cast<float*>(P(lay.Gcat));
   float* Qs = Bcat + mp;               // S x m_max, row pitch wcat
   float* Us = Bcat + 2 * mp + lp;      // S x lp
-  double* K = Gcat;                    // Q_s^T X
-  double* G = Gcat + mp;               // Q_s^T Q_s
-  double* h = Gcat + 2 * mp;           // Q_s^T r0
-  double* bv = Gcat + 2 * mp + lp;     // Q_s^T U-hat_s
-  k_seed_gather<<<rw_blocks((int64_t)S * 32, 256), 256, 0, st>>>(
+  float* K = Gcat;                     // Q_s^T X
+  float* G = Gcat + mp;                // Q_s^T Q_s
+  float* h = Gcat + 2 * mp;            // Q_s^T r0
+  float* bv = Gcat + 2 * mp + lp;      // Q_s^T U-hat_s
+  RW_LAUNCH(k_seed_gather, rw_blocks((int64_t)S * 32, 256), 256, 0, st, 
       seed_idx_dev, seed_lab_dev, S, L, lp, g->N, b->Q32, b->ld32, mp, seedlab, g->cw, g->d,
       g->sq, g->normalized, g->kind, g->ndim, g->dims[0], g->dims[1], g->dims[2], g->rowptr,
       g->col, g->ccsr, (float)gamma, Bcat, wcat);
-  RW_LAUNCH_CHECK();
-  RW_TRY(rw_gram(Qs, wcat, Bcat, wcat, S, m_max, wcat, Gcat, wcat, false, st));
+  RW_TRY(seed_gram(Qs, wcat, Bcat, wcat, S, m_max, wcat, Gcat, wcat, st));
   double* fu = reinterpret_cast<double*>(P(lay.fu));
   double* fsel = fu + (size_t)(ncand + 1) * RW_MAX_LABELS;
   RW_TRY(mark(2));
@@ -1526,26 +1884,26 @@ extern "C" rw_status rw_solve(const rw_graph* g, const rw_basis* b, const int32_
     const size_t shm = sizeof(float) * ((size_t)m_max * (m_max | 1) + 3 * (size_t)L * m_max);
     if (lp == 4) {
       cudaFuncSetAttribute(k_adapt<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
-      k_adapt<4><<<1, 256, shm, st>>>(G, wcat, bv, wcat, Qs, wcat, Us, wcat, S, L, m_max, m_step,
+      RW_LAUNCH((k_adapt<4>), 1, 256, shm, st, G, wcat, bv, wcat, Qs, wcat, Us, wcat, S, L, m_max, m_step,
                                       rho, fmax, mdev, fsel);
     } else if (lp == 8) {
       cudaFuncSetAttribute(k_adapt<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
-      k_adapt<8><<<1, 256, shm, st>>>(G, wcat, bv, wcat, Qs, wcat, Us, wcat, S, L, m_max, m_step,
+      RW_LAUNCH((k_adapt<8>), 1, 256, shm, st, G, wcat, bv, wcat, Qs, wcat, Us, wcat, S, L, m_max, m_step,
                                       rho, fmax, mdev, fsel);
     } else {
       cudaFuncSetAttribute(k_adapt<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
-      k_adapt<16><<<1, 256, shm, st>>>(G, wcat, bv, wcat, Qs, wcat, Us, wcat, S, L, m_max, m_step,
+      RW_LAUNCH((k_adapt<16>), 1, 256, shm, st, G, wcat, bv, wcat, Qs, wcat, Us, wcat, S, L, m_max, m_step,
                                        rho, fmax, mdev, fsel);
     }
     RW_LAUNCH_CHECK();
   } else {
-    k_set_m<<<1, 32, 0, st>>>(mdev, m_max);
-    RW_LAUNCH_CHECK();
+    RW_LAUNCH(k_set_m, 1, 32, 0, st, mdev, m_max);
   }
   RW_TRY(mark(3));
   // Z = Q_n^T P-hat_n
   float* part = reinterpret_cast<float*>(P(lay.part));
-  double* Z = reinterpret_cast<double*>(P(lay.Z));
+  float* Z = reinterpret_cast<float*>(P(lay.Z));
+  float* lgam = Z + (size_t)mq * lp;
   int fmt = opts->basis_format;
   if (fmt == RW_BASIS_BF16 && !b->Qbf) {
     rw_basis* bm = const_cast<rw_basis*>(b);
@@ -1555,7 +1913,7 @@ extern "C" rw_status rw_solve(const rw_graph* g, const rw_basis* b, const int32_
     RW_LAUNCH_CHECK();
   }
   int ldq_e = fmt == RW_BASIS_F32 ? b->ld32 : b->ld16;
-  double zscale = fmt == RW_BASIS_F16 ? 1.0 / b->qscale : 1.0;
+  float zscale = fmt == RW_BASIS_F16 ? 1.f / b->qscale : 1.f;
   float cscale = fmt == RW_BASIS_F16 ? 1.f / b->qscale : 1.f;
   if (fmt == RW_BASIS_F16)
     RW_TRY(proj_back<__half>(lp, false, b->Q16, ldq_e, phat, seedlab, g, mdev, part, nblk, nullptr, 0.f, nullptr, nullptr, nullptr, L, st));
@@ -1563,8 +1921,8 @@ extern "C" rw_status rw_solve(const rw_graph* g, const rw_basis* b, const int32_
     RW_TRY(proj_back<__nv_bfloat16>(lp, false, b->Qbf, ldq_e, phat, seedlab, g, mdev, part, nblk, nullptr, 0.f, nullptr, nullptr, nullptr, L, st));
   else
     RW_TRY(proj_back<float>(lp, false, b->Q32, ldq_e, phat, seedlab, g, mdev, part, nblk, nullptr, 0.f, nullptr, nullptr, nullptr, L, st));
-  k_reduce_partials<<<rw_blocks((int64_t)mq * lp * 32, 256), 256, 0, st>>>(part, nblk, ldq_e, lp, mq, zscale, Z);
-  RW_LAUNCH_CHECK();
+  RW_LAUNCH(k_reduce_partials, rw_blocks((int64_t)std::max(mq * lp, m_max) * 32, 256), 256, 0, st, 
+      part, nblk, ldq_e, lp, mq, zscale, Z, b->lam, gamma, m_max, lgam);
   RW_TRY(mark(4));
   // small system
   float* C = reinterpret_cast<float*>(P(lay.C));
@@ -1573,16 +1931,16 @@ extern "C" rw_status rw_solve(const rw_graph* g, const rw_basis* b, const int32_
                  sizeof(int) * m_max;
     if (lp == 4) {
       cudaFuncSetAttribute(k_small_solve<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
-      k_small_solve<4><<<1, 256, shm, st>>>(K, wcat, h, wcat, Z, b->lam, gamma, L, lp, mq, mdev, C,
+      RW_LAUNCH((k_small_solve<4>), 1, 256, shm, st, K, wcat, h, wcat, Z, lgam, (float)gamma, L, lp, mq, mdev, C,
                                             g->status);
     } else if (lp == 8) {
       cudaFuncSetAttribute(k_small_solve<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
-      k_small_solve<8><<<1, 256, shm, st>>>(K, wcat, h, wcat, Z, b->lam, gamma, L, lp, mq, mdev, C,
+      RW_LAUNCH((k_small_solve<8>), 1, 256, shm, st, K, wcat, h, wcat, Z, lgam, (float)gamma, L, lp, mq, mdev, C,
                                             g->status);
     } else {
       cudaFuncSetAttribute(k_small_solve<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
-      k_small_solve<16><<<1, 256, shm, st>>>(K, wcat, h, wcat, Z, b->lam, gamma, L, lp, mq, mdev,
-                                             C, g->status);
+      RW_LAUNCH((k_small_solve<16>), 1, 256, shm, st, K, wcat, h, wcat, Z, lgam, (float)gamma, L, lp, mq,
+                                             mdev, C, g->status);
     }
     RW_LAUNCH_CHECK();
   }
