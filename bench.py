@@ -264,21 +264,22 @@ def smallest_steps(err_of, target, cap=4096):
     return lo
 
 
-def equal_accuracy(rw, g, b, dsets, conv, tmp, labels, flush, stream, kw, pcg_ms, pcg_iters):
+def equal_accuracy(rw, g, b, dsets, conv, tmp, labels, flush, stream, kw, pcg_ms, pcg_iters,
+                   n_labels=LABELS):
     """The eigenvector solve refined by PCG (warm start) until it is within 1e-3 max-abs of
     the converged basic RW (calibrated untimed on the first seed set), timed like the
     plain-PCG competitor at the same accuracy."""
     si0, sl0 = dsets[0]
 
     def err_of(k):
-        rw.rw_solve(g, b, si0, sl0, LABELS, tmp, labels, refine_mode=rw.RW_REFINE_PCG,
+        rw.rw_solve(g, b, si0, sl0, n_labels, tmp, labels, refine_mode=rw.RW_REFINE_PCG,
                     want_info=False, **{**kw, "refine_steps": k})
         return float((tmp - conv).abs().max())
     k = smallest_steps(err_of, 1e-3)
     if k is None:
         return {"target_maxabs": 1e-3, "fast_pcg_refine_steps": None}
     count = min(len(dsets), 10)
-    ms = time_steps(lambda i: rw.rw_solve(g, b, dsets[i][0], dsets[i][1], LABELS, tmp, labels,
+    ms = time_steps(lambda i: rw.rw_solve(g, b, dsets[i][0], dsets[i][1], n_labels, tmp, labels,
                                           refine_mode=rw.RW_REFINE_PCG, want_info=False,
                                           **{**kw, "refine_steps": k}), count, flush, stream)
     return {"target_maxabs": 1e-3, "fast_pcg_refine_steps": k, "fast_ms": ms,
@@ -323,7 +324,8 @@ def c3_block(rw, torch, dev, flush, stream, steps=100):
                                                   want_iters=False), 10, flush, stream)
     rw.rw_solve(g, b, si0, sl0, 2, prob, lab, want_info=False, **kw)
     fast_vs_exact = float((prob - conv).abs().max())
-    equal = equal_accuracy(rw, g, b, dp, conv, tmp, lab, flush, stream, kw, pcg_ms, pcg_iters)
+    equal = equal_accuracy(rw, g, b, dp, conv, tmp, lab, flush, stream, kw, pcg_ms, pcg_iters,
+                           n_labels=2)
     rw.rw_basis_free(b)
     rw.rw_graph_free(g)
     return {"workload": "rwis-128x128x128-2label-ellipsoid", "label_maps_per_s": 1000.0 / ms,

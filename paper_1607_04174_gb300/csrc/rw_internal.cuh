@@ -94,7 +94,9 @@ struct PinnedBuf {
 enum { RW_GRAPH_GRID = 0, RW_GRAPH_CSR = 1 };
 
 struct SolveWorkspace {
-  DevBuf seedlab;   // int8 [N]: -1 unseeded, else label
+  DevBuf seedlab;   // int [N]: -1 unseeded, else label
+  DevBuf seedpart;  // seed-side sums: fit (FP64) and per-block label sums
+  bool seeds_clean = false;  // seedlab is all -1 (the last solve's final kernel cleared it)
   DevBuf small;     // small per-solve arrays (stats, Q_s, X, products, Z, C, ...)
   DevBuf xhat[2];   // refinement iterates, N x lpad FP32
   DevBuf phat;      // hat-space priors, N x lpad FP32

@@ -7,17 +7,18 @@
 // unnormalized Laplacian sq = s = 1.  Operator coefficients c_ij = w_ij s_i s_j, so the seeded
 // block of L-hat is B-hat_ij = -c_ij.
 //
-// Per solve (S seeds, m_max basis columns, l labels):
-//   scatter seeds, Gaussian fit, P-hat (N x lp)                    -> k_seed_scatter, k_fit,
-//                                                                     k_priors
+// Per solve (S seeds, m_max basis columns, l labels), every kernel launched with programmatic
+// dependent launch (it waits on griddepcontrol before reading its predecessors' output):
+//   seed labels, Gaussian fit, P-hat (N x lp)      -> k_seed_scatter, k_priors (the fit from the
+//                                                     scatter blocks' sums in every block)
 //   Q_s, X = B-hat Q_n (S x m_max), r0 = L-hat_s U-hat_s + gamma U-hat_s  -> k_seed_gather
-//   K = Q_s^T X, h = Q_s^T r0, b = Q_s^T U-hat_s, G = Q_s^T Q_s     -> rw_gram (FP64 out)
-//   m (adaptive: one CTA per candidate m, trust-region least squares) -> k_adapt, k_pick
-//   Z = Q_n^T P-hat_n (streams the 16-bit basis once)                -> k_project, k_reduce
+//   K = Q_s^T X, h = Q_s^T r0, b = Q_s^T U-hat_s, G = Q_s^T Q_s (FP32)  -> k_seed_gram (cluster)
+//   m (incremental Cholesky over the nested candidates, trust region)  -> k_adapt
+//   Z = Q_n^T P-hat_n (streams the 16-bit basis once)  -> k_project_cw, k_reduce_partials
 //   (diag(lambda + gamma) - K) y = h + gamma K Lambda_gamma Z, C = y + gamma Lambda_gamma Z
-//                                                                    -> k_small_solve
-//   U-hat_n = Q_n C (streams the basis again)                        -> k_backproject
-//   refinement steps, U = s * U-hat, labels = argmax                 -> k_jacobi_step
+//                                                     -> k_small_solve (blocked LU)
+//   U-hat_n = Q_n C (streams the basis again)          -> k_backproject_panel
+//   refinement steps, U = s * U-hat, labels = argmax   -> k_jacobi_grid (k_jacobi_step on CSR)
 #include "rw_internal.cuh"
 
 #include <cooperative_groups.h>
@@ -29,7 +30,8 @@ namespace cg = cooperative_groups;
 
 namespace {
 
-constexpr int kMaxSmallM = 224;  // m x m FP32 factorizations live in one CTA's shared memory
+constexpr int kMaxSmallM = 224;
+constexpr int kMaxSeeds = 65536;   // seeds per solve (the validation's limit)  // m x m FP32 factorizations live in one CTA's shared memory
 
 int lpad_of(int L) { return L <= 4 ? 4 : (L <= 8 ? 8 : 16); }
 
@@ -73,86 +75,140 @@ __global__ void k_seed_reset(int* __restrict__ seedlab, int64_t n, double* __res
   rw_grid_trigger();
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) seedlab[i] = -1;
-  if (i < nstats) stats[i] = 0.0;
+  if (stats && i < nstats) stats[i] = 0.0;
 }
 
-__global__ void k_seed_scatter(const int32_t* __restrict__ idx, const int32_t* __restrict__ lab,
-                               int S, int L, int64_t N, const float* __restrict__ J,
-                               int* __restrict__ seedlab, double* __restrict__ stats,
-                               int* status) {
+// Marks the seeds (an index or label out of range or a voxel seeded twice sets a status bit)
+// and writes, per block and label, the count, the mean and the sum of squared deviations from
+// that mean of the seed intensities: bpart[block][3 k + {0, 1, 2}].  One warp per label, two
+// passes (mean, then deviations) with fixed butterflies, so there is no cancellation and the
+// result does not depend on scheduling.
+__global__ void __launch_bounds__(256)
+k_seed_scatter(const int32_t* __restrict__ idx, const int32_t* __restrict__ lab, int S, int L,
+               int64_t N, const float* __restrict__ J, int* __restrict__ seedlab,
+               float* __restrict__ bpart, int* status) {
   rw_grid_wait();
   rw_grid_trigger();
-  int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= S) return;
-  int i = idx[t], k = lab[t];
-  if (i < 0 || (int64_t)i >= N || k < 0 || k >= L) {
-    atomicOr(status, RW_DEV_BAD_SEED);
-    return;
+  __shared__ int sk[256];
+  __shared__ float sv[256];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  const int t = blockIdx.x * blockDim.x + tid;
+  int k = -1;
+  float v = 0.f;
+  if (t < S) {
+    const int i = idx[t];
+    k = lab[t];
+    if (i < 0 || (int64_t)i >= N || k < 0 || k >= L) {
+      atomicOr(status, RW_DEV_BAD_SEED);
+      k = -1;
+    } else {
+      if (atomicCAS(&seedlab[i], -1, k) != -1) atomicOr(status, RW_DEV_DUP_SEED);
+      v = J ? J[i] : 0.f;
+    }
   }
-  int old = atomicCAS(&seedlab[i], -1, k);
-  if (old != -1) {
-    atomicOr(status, RW_DEV_DUP_SEED);
-    return;
+  sk[tid] = k;
+  sv[tid] = v;
+  __syncthreads();
+  for (int kk = warp; kk < L; kk += nw) {
+    float sum = 0.f, cnt = 0.f;
+    for (int e = lane; e < 256; e += 32)
+      if (sk[e] == kk) { sum += sv[e]; cnt += 1.f; }
+    sum = warp_sum(sum);
+    cnt = warp_sum(cnt);
+    const float mean = cnt > 0.f ? sum / cnt : 0.f;
+    float m2 = 0.f;
+    for (int e = lane; e < 256; e += 32)
+      if (sk[e] == kk) { const float d = sv[e] - mean; m2 = fmaf(d, d, m2); }
+    m2 = warp_sum(m2);
+    if (lane == 0) {
+      float* o = bpart + ((size_t)blockIdx.x * L + kk) * 3;
+      o[0] = cnt;
+      o[1] = mean;
+      o[2] = m2;
+    }
   }
-  double v = J ? (double)J[i] : 0.0;
-  atomicAdd(&stats[3 * k + 0], v);
-  atomicAdd(&stats[3 * k + 1], v * v);
-  atomicAdd(&stats[3 * k + 2], 1.0);
 }
 
-// mu_k, 1/(2 sigma_k^2), log sigma_k with sigma_k = max(std, 1e-3) (ML estimates, Sec. IV-A)
-__global__ void k_fit(const double* __restrict__ stats, int L, int prior_mode,
-                      float* __restrict__ fit, double* __restrict__ fit64, int* status) {
-  rw_grid_wait();
-  rw_grid_trigger();
-  int k = threadIdx.x;
+// The Gaussian fit of Sec. IV-A from the scatter blocks' (count, mean, squared deviations),
+// merged in block order with the pairwise update of the mean and the sum of squared
+// deviations: mu_k, 1/(2 sigma_k^2), log sigma_k with sigma_k = max(std, 1e-3) (maximum
+// likelihood: the variance divides by the count).
+__device__ void seed_fit(const float* __restrict__ bpart, int nsb, int L, int prior_mode,
+                         float* fit, double* fit64, int* status) {
+  const int k = threadIdx.x;
   if (k >= L) return;
-  double n = stats[3 * k + 2];
-  if (n <= 0.0) {
-    if (prior_mode == 0) atomicOr(status, RW_DEV_EMPTY_LABEL);
+  float n = 0.f, mean = 0.f, m2 = 0.f;
+  for (int b = 0; b < nsb; ++b) {
+    const float* o = bpart + ((size_t)b * L + k) * 3;
+    const float nb = o[0];
+    if (nb > 0.f) {
+      const float nt = n + nb, delta = o[1] - mean;
+      mean += delta * (nb / nt);
+      m2 += o[2] + delta * delta * (n * nb / nt);
+      n = nt;
+    }
+  }
+  if (!(n > 0.f)) {
+    if (prior_mode == 0 && status) atomicOr(status, RW_DEV_EMPTY_LABEL);
     fit[k] = 0.f; fit[16 + k] = 0.f; fit[32 + k] = 0.f;
-    fit64[k] = 0.0; fit64[16 + k] = 0.0;
+    if (fit64) { fit64[k] = 0.0; fit64[16 + k] = 0.0; }
     return;
   }
-  double mu = stats[3 * k] / n;
-  double var = stats[3 * k + 1] / n - mu * mu;
-  double sig = fmax(sqrt(fmax(var, 0.0)), 1e-3);
-  fit[k] = (float)mu;
-  fit[16 + k] = (float)(0.5 / (sig * sig));
-  fit[32 + k] = (float)log(sig);
-  fit64[k] = mu;
-  fit64[16 + k] = sig;
+  const float sig = fmaxf(sqrtf(fmaxf(m2 / n, 0.f)), 1e-3f);
+  fit[k] = mean;
+  fit[16 + k] = 0.5f / (sig * sig);
+  fit[32 + k] = logf(sig);
+  if (fit64) { fit64[k] = mean; fit64[16 + k] = sig; }
 }
 
 // P-hat rows (N x lp): Gaussian priors normalized per voxel, or caller priors, times d^{1/2}
-__global__ void k_priors(const float* __restrict__ J, const float* __restrict__ sq, int64_t N,
-                         int L, int lp, int prior_mode, const float* __restrict__ fit,
-                         const float* __restrict__ Pin, float* __restrict__ phat, int* status) {
+template <int LP>
+__global__ void __launch_bounds__(256)
+k_priors(const float* __restrict__ J, const float* __restrict__ sq, int64_t N, int L,
+         int prior_mode, const float* __restrict__ bpart, int nsb, double* __restrict__ fit64,
+         const float* __restrict__ Pin, float* __restrict__ phat, int* status) {
   rw_grid_wait();
   rw_grid_trigger();
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  __shared__ float fit[48];
+  if (prior_mode == 0)
+    seed_fit(bpart, nsb, L, prior_mode, fit, blockIdx.x == 0 ? fit64 : nullptr,
+             blockIdx.x == 0 ? status : nullptr);
+  else if (blockIdx.x == 0)
+    seed_fit(bpart, nsb, L, prior_mode, fit, fit64, nullptr);
+  __syncthreads();
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
-  float p[RW_MAX_LABELS];
+  float p[LP];
   if (prior_mode == 0) {
-    float x = J[i], mx = -INFINITY;
-    for (int k = 0; k < L; ++k) {
-      float t = x - fit[k];
-      p[k] = -t * t * fit[16 + k] - fit[32 + k];
+    const float x = J[i];
+    float mx = -INFINITY;
+#pragma unroll
+    for (int k = 0; k < LP; ++k) {
+      const float t = x - fit[k];
+      p[k] = (k < L) ? -t * t * fit[16 + k] - fit[32 + k] : -INFINITY;
       mx = fmaxf(mx, p[k]);
     }
     float sum = 0.f;
-    for (int k = 0; k < L; ++k) { p[k] = expf(p[k] - mx); sum += p[k]; }
-    float inv = 1.f / sum;
-    for (int k = 0; k < L; ++k) p[k] *= inv;
+#pragma unroll
+    for (int k = 0; k < LP; ++k) {
+      p[k] = (k < L) ? __expf(p[k] - mx) : 0.f;
+      sum += p[k];
+    }
+    const float inv = 1.f / sum;
+#pragma unroll
+    for (int k = 0; k < LP; ++k) p[k] *= inv;
   } else {
-    for (int k = 0; k < L; ++k) {
-      p[k] = Pin[i * L + k];
-      if (!isfinite(p[k])) atomicOr(status, RW_DEV_NONFINITE);
+#pragma unroll
+    for (int k = 0; k < LP; ++k) {
+      p[k] = (k < L) ? Pin[i * L + k] : 0.f;
+      if (k < L && !isfinite(p[k])) atomicOr(status, RW_DEV_NONFINITE);
     }
   }
-  float r = sq[i];
-  float* o = phat + i * lp;
-  for (int k = 0; k < lp; ++k) o[k] = (k < L) ? r * p[k] : 0.f;
+  const float r = sq[i];
+  float4* o = reinterpret_cast<float4*>(phat + i * LP);
+#pragma unroll
+  for (int k4 = 0; k4 < LP / 4; ++k4)
+    o[k4] = make_float4(r * p[4 * k4], r * p[4 * k4 + 1], r * p[4 * k4 + 2], r * p[4 * k4 + 3]);
 }
 
 // One warp per seed: Q_s row, X = B-hat Q_n row, U-hat_s row, r0 = L-hat_s U-hat_s + g U-hat_s
@@ -215,12 +271,12 @@ __global__ void k_seed_gather(const int32_t* __restrict__ idx, const int32_t* __
 // Shared-memory FP32 dense kernels for one CTA (row stride ms, odd, so column walks are free
 // of bank conflicts).
 // ---------------------------------------------------------------------------------------
-// A[i][j] -= sum_{q < kb} A[i][p0 + q] A[p0 + q][j] for i, j in [r1, m): warp tasks of 8 rows x
-// 128 columns (lane = column within each 32-column group), k unrolled by 2 for ILP
-__device__ void gemm_trailing(float* A, int ms, int m, int r1, int p0, int kb) {
+// A[i][j] -= sum_{q < kb} A[i][p0 + q] A[p0 + q][j] for i in [r1, m), j in [r1, ncol): warp tasks
+// of 8 rows x 128 columns (lane = column within each 32-column group), k unrolled by 2 for ILP
+__device__ void gemm_trailing(float* A, int ms, int m, int ncol, int r1, int p0, int kb) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const int n = m - r1;
-  const int nrt = (n + 7) / 8, nct = (n + 127) / 128;
+  const int n = m - r1, nc = ncol - r1;
+  const int nrt = (n + 7) / 8, nct = (nc + 127) / 128;
   for (int task = warp; task < nrt * nct; task += nw) {
     const int i0 = r1 + 8 * (task / nct), j0 = r1 + 128 * (task % nct) + lane;
     float acc[8][4];
@@ -235,7 +291,7 @@ __device__ void gemm_trailing(float* A, int ms, int m, int r1, int p0, int kb) {
 #pragma unroll
       for (int u = 0; u < 8; ++u) av[u] = A[min(i0 + u, ilast) * ms + p0 + q];
 #pragma unroll
-      for (int v = 0; v < 4; ++v) bv[v] = A[(p0 + q) * ms + min(j0 + 32 * v, ilast)];
+      for (int v = 0; v < 4; ++v) bv[v] = A[(p0 + q) * ms + min(j0 + 32 * v, ncol - 1)];
 #pragma unroll
       for (int u = 0; u < 8; ++u)
 #pragma unroll
@@ -246,31 +302,15 @@ __device__ void gemm_trailing(float* A, int ms, int m, int r1, int p0, int kb) {
 #pragma unroll
       for (int v = 0; v < 4; ++v) {
         const int i = i0 + u, j = j0 + 32 * v;
-        if (i < m && j < m) A[i * ms + j] -= acc[u][v];
+        if (i < m && j < ncol) A[i * ms + j] -= acc[u][v];
       }
   }
 }
 
-// one warp: x = U^{-1} L^{-1} b for the LU held in A (unit lower below the diagonal, U on and
-// above it; uinv = 1 / diag(U)).  Lane t keeps entries t + 32 q (m <= 224) in registers; each
-// newly final entry is broadcast by shuffle.  The register group of the pivot is a
-// compile-time index (outer loop unrolled over groups), so a step is one shuffle and a few
-// independent FMAs.
-template <int QJ>
-__device__ __forceinline__ void lu_fwd_group(const float* A, int m, int ms, float (&y)[7], int lane) {
-  if (32 * QJ < m) {
-    const int jend = min(32, m - 32 * QJ);
-    for (int lj = 0; lj < jend; ++lj) {
-      const int j = 32 * QJ + lj;
-      const float yj = __shfl_sync(0xffffffff, y[QJ], lj);
-#pragma unroll
-      for (int q = QJ; q < 7; ++q) {
-        const int i = lane + 32 * q;
-        if (i > j && i < m) y[q] = fmaf(-A[i * ms + j], yj, y[q]);
-      }
-    }
-  }
-}
+// one warp: U x = y for the upper factor held in A (uinv = 1 / diag(U)), one register group of
+// 32 rows at a time.  Lane t keeps entries t + 32 q (m <= 224) in registers; each newly final
+// entry is broadcast by shuffle.  The register group of the pivot is a compile-time index, so a
+// step is one shuffle and a few independent FMAs.
 template <int QI>
 __device__ __forceinline__ void lu_bwd_group(const float* A, int m, int ms, const float* uinv,
                                              float (&y)[7], int lane) {
@@ -287,32 +327,6 @@ __device__ __forceinline__ void lu_bwd_group(const float* A, int m, int ms, cons
     }
   }
 }
-__device__ void lu_solve_warp(const float* A, int m, int ms, const float* uinv, const float* b,
-                              float* x) {
-  const int lane = threadIdx.x & 31;
-  float y[7];
-#pragma unroll
-  for (int q = 0; q < 7; ++q) y[q] = (lane + 32 * q < m) ? b[lane + 32 * q] : 0.f;
-  lu_fwd_group<0>(A, m, ms, y, lane);
-  lu_fwd_group<1>(A, m, ms, y, lane);
-  lu_fwd_group<2>(A, m, ms, y, lane);
-  lu_fwd_group<3>(A, m, ms, y, lane);
-  lu_fwd_group<4>(A, m, ms, y, lane);
-  lu_fwd_group<5>(A, m, ms, y, lane);
-  lu_fwd_group<6>(A, m, ms, y, lane);
-  lu_bwd_group<6>(A, m, ms, uinv, y, lane);
-  lu_bwd_group<5>(A, m, ms, uinv, y, lane);
-  lu_bwd_group<4>(A, m, ms, uinv, y, lane);
-  lu_bwd_group<3>(A, m, ms, uinv, y, lane);
-  lu_bwd_group<2>(A, m, ms, uinv, y, lane);
-  lu_bwd_group<1>(A, m, ms, uinv, y, lane);
-  lu_bwd_group<0>(A, m, ms, uinv, y, lane);
-#pragma unroll
-  for (int q = 0; q < 7; ++q)
-    if (lane + 32 * q < m) x[lane + 32 * q] = y[q];
-  __syncwarp();
-}
-
 // ---------------------------------------------------------------------------------------
 // Compact single-warp factorizations of a 32 x 32 diagonal block.  Lane r keeps the not yet
 // final part of row r in registers, shifted so that a[0] is always the current column: one
@@ -375,7 +389,8 @@ __device__ void chol_diag_rot(float* A, int ms, int k0, int kb, float* dinv, flo
 // multipliers below the diagonal, U on and above it; uinv[k0 + c] = 1 / U_cc.  Row kk is
 // broadcast from lane kk by shuffles (one per register of the shifted row).  Also writes the
 // shifted copies used by the panel solves: Ush[c][t] = U_c,c+1+t and Lsh[c][t] = L_c+1+t,c
-// (32 x 32 each, zero outside the block).  A pivot below 1e-3 |dref| sets *unstable.
+// (32 x 32 each, zero outside the block).  A pivot below 1e-3 dref (the original row scale) sets
+// *unstable.
 __device__ void lu_diag_rot(float* A, int ms, int k0, int kb, float* buf, const float* dref,
                             float* uinv, float* Ush, float* Lsh, int* unstable) {
   (void)buf;
@@ -1002,20 +1017,24 @@ __global__ void k_set_m(int* mdev, int m) {
 template <typename T> struct Vec16;
 template <> struct Vec16<__half> {
   static constexpr int V = 8;
-  __device__ static void load(const __half* p, float* o) {
-    uint4 u = __ldg(reinterpret_cast<const uint4*>(p));
+  __device__ static void unpack(const uint4& u, float* o) {
     const __half2* h = reinterpret_cast<const __half2*>(&u);
 #pragma unroll
     for (int t = 0; t < 4; ++t) { float2 f = __half22float2(h[t]); o[2 * t] = f.x; o[2 * t + 1] = f.y; }
   }
+  __device__ static void load(const __half* p, float* o) {
+    unpack(__ldg(reinterpret_cast<const uint4*>(p)), o);
+  }
 };
 template <> struct Vec16<__nv_bfloat16> {
   static constexpr int V = 8;
-  __device__ static void load(const __nv_bfloat16* p, float* o) {
-    uint4 u = __ldg(reinterpret_cast<const uint4*>(p));
+  __device__ static void unpack(const uint4& u, float* o) {
     const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&u);
 #pragma unroll
     for (int t = 0; t < 4; ++t) { float2 f = __bfloat1622float2(h[t]); o[2 * t] = f.x; o[2 * t + 1] = f.y; }
+  }
+  __device__ static void load(const __nv_bfloat16* p, float* o) {
+    unpack(__ldg(reinterpret_cast<const uint4*>(p)), o);
   }
 };
 template <> struct Vec16<float> {
@@ -1134,8 +1153,9 @@ __global__ void k_reduce_partials(const float* __restrict__ part, int nblk, int 
 //   M = diag(lambda + gamma) - K_m,  M y = h + gamma K (Lambda_gamma Z),  C = y + gamma Lambda_gamma Z
 // LU in FP32 shared memory.  M is diagonally dominant in practice (its off-diagonal part is
 // Q_s^T X, small next to lambda + gamma), so the elimination first runs without pivoting,
-// blocked by 32-column panels.  If a pivot falls below 1e-3 of its original diagonal entry, M
-// is reloaded and eliminated with partial pivoting (rows permuted through an index array).
+// blocked by 32-column panels.  If a pivot falls below 1e-3 of the largest entry of its
+// original row, M is reloaded and eliminated with partial pivoting (rows permuted through an
+// index array).
 // ---------------------------------------------------------------------------------------
 __device__ void load_M(float* M, int m, int ms, const float* __restrict__ K, int ldk,
                        const float* __restrict__ lgam) {
@@ -1168,13 +1188,14 @@ k_small_solve(const float* __restrict__ K, int ldk, const float* __restrict__ h,
   rw_grid_trigger();
   extern __shared__ float sm[];
   const int m = mdev[0];
-  const int ms = m | 1;
-  float* M = sm;                       // m x ms
+  const int na = m + L;                // augmented columns: [M | B]
+  const int ms = na | 1;
+  float* M = sm;                       // m x ms : M, then the right-hand sides in columns m..
   float* W = M + (size_t)m * ms;       // m x L : Lambda_gamma Z (row-major)
-  float* B = W + (size_t)m * L;        // L x m : right-hand sides (label-major)
-  float* Y = B + (size_t)m * L;        // L x m : solution (label-major)
-  int* perm = reinterpret_cast<int*>(Y + (size_t)m * L);  // m
-  float* dref = reinterpret_cast<float*>(perm + m);       // m : |M_ii| before elimination
+  float* B = W + (size_t)m * L;        // L x m : right-hand sides (label-major), kept for the
+                                       //         pivoting fallback
+  int* perm = reinterpret_cast<int*>(B + (size_t)m * L);  // m
+  float* dref = reinterpret_cast<float*>(perm + m);       // m : row scales before elimination
   __shared__ float uinv[kMaxSmallM];
   __shared__ __align__(16) float buf[128];
   __shared__ __align__(16) float Ush[32 * 32], Lsh[32 * 32];
@@ -1189,13 +1210,17 @@ k_small_solve(const float* __restrict__ K, int ldk, const float* __restrict__ h,
   }
   load_M(M, m, ms, K, ldk, lgam);
   __syncthreads();
-  for (int i = threadIdx.x; i < m; i += blockDim.x) {
-    perm[i] = i;
-    dref[i] = fabsf(M[i * ms + i]);  // |M_ii| before elimination
+  for (int i = threadIdx.x; i < m; i += blockDim.x) perm[i] = i;
+  for (int i = warp; i < m; i += nty) {  // row scale max_j |M_ij| before elimination
+    float mx = 0.f;
+    for (int j = lane; j < m; j += 32) mx = fmaxf(mx, fabsf(M[(size_t)i * ms + j]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffff, mx, o));
+    if (lane == 0) dref[i] = mx;
   }
-  __syncthreads();
   // B += gamma K W, with K read back from the shared copy of M (K_ij = -M_ij off the diagonal,
-  // K_ii = lambda_i + gamma - M_ii): one thread per (row, label), the row walked in order
+  // K_ii = lambda_i + gamma - M_ii): one thread per (row, label), the row walked in order; the
+  // result also goes to the augmented columns of M
   for (int e = threadIdx.x; e < m * L; e += blockDim.x) {
     const int i = e % m, k = e / m;
     const float* mi = M + (size_t)i * ms;
@@ -1207,29 +1232,56 @@ k_small_solve(const float* __restrict__ K, int ldk, const float* __restrict__ h,
     }
     if (j < m) acc0 = fmaf(-mi[j], W[j * L + k], acc0);
     const float kii_extra = lgam[i] * W[i * L + k];   // diagonal: K_ii = lgam_i - M_ii
-    B[k * m + i] += gamma * (acc0 + acc1 + kii_extra);
+    const float rhs = B[k * m + i] + gamma * (acc0 + acc1 + kii_extra);
+    B[k * m + i] = rhs;
+    M[(size_t)i * ms + m + k] = rhs;
   }
   __syncthreads();
-  // blocked LU without pivoting, 32-column panels: the diagonal block on one warp in
-  // registers, the two triangular solves one row / column per thread, the trailing update in
-  // 4 x 4 register tiles
+  // blocked LU without pivoting of [M | B], 32-column panels: the diagonal block on one warp
+  // in registers, the two triangular solves one row / column per thread (the column solves
+  // also cover the right-hand sides), the trailing update in 8 x 4 register tiles.  The
+  // right-hand-side columns end as L^{-1} B, so only the upper solve remains.
   for (int p0 = 0; p0 < m; p0 += 32) {
     const int kb = min(32, m - p0);
     if (warp == 0) lu_diag_rot(M, ms, p0, kb, buf, dref, uinv, Ush, Lsh, &unstable);
     __syncthreads();
-    const int r1 = p0 + kb, n = m - r1;
+    const int r1 = p0 + kb, n = m - r1, nc = na - r1;
+    for (int t = threadIdx.x; t < n + nc; t += blockDim.x) {
+      if (t < n) trsm_row_rot(M + (size_t)(r1 + t) * ms + p0, kb, Ush, uinv + p0);
+      else trsm_col_rot(M + (size_t)p0 * ms + r1 + (t - n), ms, kb, Lsh);
+    }
+    __syncthreads();
     if (n > 0) {
-      for (int t = threadIdx.x; t < 2 * n; t += blockDim.x) {
-        if (t < n) trsm_row_rot(M + (size_t)(r1 + t) * ms + p0, kb, Ush, uinv + p0);
-        else trsm_col_rot(M + (size_t)p0 * ms + r1 + (t - n), ms, kb, Lsh);
-      }
-      __syncthreads();
-      gemm_trailing(M, ms, m, r1, p0, kb);
+      gemm_trailing(M, ms, m, na, r1, p0, kb);
       __syncthreads();
     }
   }
   if (!unstable) {
-    for (int k = warp; k < L; k += nty) lu_solve_warp(M, m, ms, uinv, B + (size_t)k * m, Y + (size_t)k * m);
+    // U x = y per label (warp per label); C = x + gamma Lambda_gamma Z written directly
+    for (int k = warp; k < L; k += nty) {
+      float y[7];
+#pragma unroll
+      for (int q = 0; q < 7; ++q) {
+        const int i = lane + 32 * q;
+        y[q] = i < m ? M[(size_t)i * ms + m + k] : 0.f;
+      }
+      lu_bwd_group<6>(M, m, ms, uinv, y, lane);
+      lu_bwd_group<5>(M, m, ms, uinv, y, lane);
+      lu_bwd_group<4>(M, m, ms, uinv, y, lane);
+      lu_bwd_group<3>(M, m, ms, uinv, y, lane);
+      lu_bwd_group<2>(M, m, ms, uinv, y, lane);
+      lu_bwd_group<1>(M, m, ms, uinv, y, lane);
+      lu_bwd_group<0>(M, m, ms, uinv, y, lane);
+#pragma unroll
+      for (int q = 0; q < 7; ++q) {
+        const int i = lane + 32 * q;
+        if (i < m) C[(size_t)i * lp + k] = y[q] + gamma * W[i * L + k];
+      }
+    }
+    for (int e = threadIdx.x; e < mq * lp; e += blockDim.x) {  // padding rows / labels
+      const int i = e / lp, k = e % lp;
+      if (i >= m || k >= L) C[e] = 0.f;
+    }
   } else {
     // a pivot fell below 1e-3 of its original diagonal: partial pivoting from the original M
     __syncthreads();
@@ -1268,10 +1320,16 @@ k_small_solve(const float* __restrict__ K, int ldk, const float* __restrict__ h,
     for (int i = threadIdx.x; i < m; i += blockDim.x) uinv[i] = 1.f / M[perm[i] * ms + i];
     __syncthreads();
     // forward (unit lower, multipliers a_ij / u_jj) and backward (upper) substitution on the
-    // permuted rows, one warp per label
+    // permuted rows, one warp per label, in place in B's row for the label (the original
+    // right-hand sides are first moved to row order by a copy into the augmented columns)
+    for (int e = threadIdx.x; e < m * L; e += blockDim.x) {
+      const int i = e % m, k = e / m;
+      M[(size_t)i * ms + m + k] = B[k * m + perm[i]];
+    }
+    __syncthreads();
     for (int k = warp; k < L; k += nty) {
-      float* y = Y + (size_t)k * m;
-      for (int i = lane; i < m; i += 32) y[i] = B[(size_t)k * m + perm[i]];
+      float* y = B + (size_t)k * m;
+      for (int i = lane; i < m; i += 32) y[i] = M[(size_t)i * ms + m + k];
       __syncwarp();
       for (int j = 0; j < m; ++j) {
         const float f = y[j] * uinv[j];
@@ -1286,13 +1344,13 @@ k_small_solve(const float* __restrict__ K, int ldk, const float* __restrict__ h,
         __syncwarp();
       }
     }
-  }
-  __syncthreads();
-  for (int e = threadIdx.x; e < mq * lp; e += blockDim.x) {
-    int i = e / lp, k = e % lp;
-    float v = 0.f;
-    if (i < m && k < L) v = Y[(size_t)k * m + i] + gamma * W[i * L + k];
-    C[e] = v;
+    __syncthreads();
+    for (int e = threadIdx.x; e < mq * lp; e += blockDim.x) {
+      const int i = e / lp, k = e % lp;
+      float v = 0.f;
+      if (i < m && k < L) v = B[(size_t)k * m + i] + gamma * W[i * L + k];
+      C[e] = v;
+    }
   }
   if (threadIdx.x == 0 && bad) atomicOr(status, RW_DEV_SINGULAR);
 }
@@ -1310,7 +1368,7 @@ __global__ void __launch_bounds__(256)
 k_backproject(const T* __restrict__ Q, int ldq, int cpr, const float* __restrict__ Cg,
               float cscale, const int* __restrict__ seedlab, const float* __restrict__ sq,
               const float* __restrict__ s, int64_t N, int L, const int* __restrict__ mdev,
-              float* __restrict__ xhat, float* __restrict__ U, uint8_t* __restrict__ labels) {
+              float* __restrict__ xhat, float* __restrict__ U, uint8_t* __restrict__ labels, int* clear_seedlab) {
   rw_grid_wait();
   rw_grid_trigger();
   constexpr int V = Vec16<T>::V;
@@ -1392,6 +1450,7 @@ k_backproject(const T* __restrict__ Q, int ldq, int cpr, const float* __restrict
         }
         if (writer && k == 0) labels[i] = (uint8_t)best;
       }
+      if (clear_seedlab && writer && k == 0 && sl >= 0) clear_seedlab[i] = -1;
     }
   }
 }
@@ -1480,6 +1539,101 @@ k_project_panel(const T* __restrict__ Qp, int64_t N, int nchunk_max,
   }
 }
 
+// Z partials on the panel layout, chunk-major: a block owns a range of rows, split into
+// kParts parts; warps take (chunk, part) items, a lane walks the item's rows (8 rows of 16 bytes
+// in flight per lane) and keeps the 8 x LPG products of one label group in registers; a single
+// reduce-scatter butterfly per item, then the parts are added in part order in shared memory.
+// Block partials part[block][8 c + v][k] (the layout k_reduce_partials reads).
+constexpr int kParts = 4;
+
+// butterfly: after it, lane j holds the warp sum of val[j] (val has 32 entries)
+__device__ __forceinline__ float reduce_scatter32(float (&val)[32], int lane) {
+#pragma unroll
+  for (int half = 16, off = 16; half >= 1; half >>= 1, off >>= 1) {
+    const bool up = (lane & off) != 0;
+#pragma unroll
+    for (int t = 0; t < half; ++t) {
+      const float send = up ? val[t] : val[t + half];
+      const float keep = up ? val[t + half] : val[t];
+      val[t] = keep + __shfl_xor_sync(0xffffffff, send, off);
+    }
+  }
+  return val[0];
+}
+
+template <typename T, int LP>
+__global__ void __launch_bounds__(256, 2)
+k_project_cw(const T* __restrict__ Qp, int64_t N, int nchunk_max, const float* __restrict__ phat,
+             const int* __restrict__ seedlab, const int* __restrict__ mdev, int64_t rows_per_block,
+             float* __restrict__ part) {
+  rw_grid_wait();
+  rw_grid_trigger();
+  constexpr int LPG = LP < 4 ? LP : 4;   // labels per pass: 8 x 4 = 32 products per lane
+  constexpr int NG = LP / LPG;
+  extern __shared__ float red[];        // kParts x nchunk_max x 8 x LP
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int m = mdev[0];
+  const int nch = min((m + 7) / 8, nchunk_max);
+  const int64_t r0 = (int64_t)blockIdx.x * rows_per_block;
+  const int64_t r1 = min(N, r0 + rows_per_block);
+  const int64_t plen = (r1 - r0 + kParts - 1) / kParts;
+  const int items = nch * kParts * NG;
+  for (int it = warp; it < items; it += nw) {
+    const int c = it % nch, rest = it / nch, pt = rest % kParts, g = rest / kParts;
+    const int64_t a0 = r0 + pt * plen, a1 = min(r1, a0 + plen);
+    const T* qc = Qp + (int64_t)c * N * 8;
+    float acc[32];
+#pragma unroll
+    for (int t = 0; t < 32; ++t) acc[t] = 0.f;
+    for (int64_t i0 = a0 + lane; i0 < a1; i0 += 32 * 8) {
+      uint4 raw[8];            // 8 rows of this chunk in flight, converted at use
+      float p[8][LPG];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int64_t i = i0 + 32 * u;
+        bool use = i < a1;
+        if (use) use = __ldg(seedlab + i) < 0;
+        raw[u] = use ? __ldg(reinterpret_cast<const uint4*>(qc + i * 8)) : make_uint4(0, 0, 0, 0);
+        if (use) {
+          if constexpr (LPG == 4) {
+            const float4 pv = __ldg(reinterpret_cast<const float4*>(phat + i * LP + g * LPG));
+            p[u][0] = pv.x; p[u][1] = pv.y; p[u][2] = pv.z; p[u][3] = pv.w;
+          } else {
+#pragma unroll
+            for (int k = 0; k < LPG; ++k) p[u][k] = __ldg(phat + i * LP + g * LPG + k);
+          }
+        } else {
+#pragma unroll
+          for (int k = 0; k < LPG; ++k) p[u][k] = 0.f;
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        float q[8];
+        Vec16<T>::unpack(raw[u], q);
+#pragma unroll
+        for (int v = 0; v < 8; ++v)
+#pragma unroll
+          for (int k = 0; k < LPG; ++k) acc[v * LPG + k] = fmaf(q[v], p[u][k], acc[v * LPG + k]);
+      }
+    }
+    const float sum = reduce_scatter32(acc, lane);  // lane j: product j = (v = j / LPG, k = j % LPG)
+    if (lane < 8 * LPG) {
+      const int v = lane / LPG, k = lane % LPG;
+      red[((size_t)pt * nchunk_max + c) * 8 * LP + v * LP + g * LPG + k] = sum;
+    }
+  }
+  __syncthreads();
+  float* pb = part + (int64_t)blockIdx.x * nchunk_max * 8 * LP;
+  for (int e = threadIdx.x; e < nchunk_max * 8 * LP; e += blockDim.x) {
+    const int c = e / (8 * LP);
+    float v = 0.f;
+    if (c < nch)
+      for (int pt = 0; pt < kParts; ++pt) v += red[(size_t)pt * nchunk_max * 8 * LP + e];
+    pb[e] = v;
+  }
+}
+
 // U-hat_n = Q_n C on the panel layout: lane = row, the chunk's 8 x LP coefficients come from
 // shared memory as broadcasts; no cross-lane reduction.
 template <typename T, int LP>
@@ -1488,13 +1642,15 @@ k_backproject_panel(const T* __restrict__ Qp, int64_t N, int nchunk_max,
                     const float* __restrict__ Cg, float cscale, const int* __restrict__ seedlab,
                     const float* __restrict__ sq, const float* __restrict__ s, int L,
                     const int* __restrict__ mdev, float* __restrict__ xhat,
-                    float* __restrict__ U, uint8_t* __restrict__ labels) {
+                    float* __restrict__ U, uint8_t* __restrict__ labels, int* clear_seedlab) {
   rw_grid_wait();
   rw_grid_trigger();
-  extern __shared__ float Cs[];  // (8 nchunk_max) x LP
+  extern __shared__ float Cs[];  // (8 nchunk_max, rounded up to 4 chunks) x LP
   const int m = mdev[0];
   const int nch = min((m + 7) / 8, nchunk_max);
-  for (int e = threadIdx.x; e < nchunk_max * 8 * LP; e += blockDim.x) Cs[e] = Cg[e] * cscale;
+  const int ncs = (nchunk_max + 3) / 4 * 4;
+  for (int e = threadIdx.x; e < ncs * 8 * LP; e += blockDim.x)
+    Cs[e] = e < nchunk_max * 8 * LP ? Cg[e] * cscale : 0.f;
   __syncthreads();
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
        i += (int64_t)gridDim.x * blockDim.x) {
@@ -1503,26 +1659,23 @@ k_backproject_panel(const T* __restrict__ Qp, int64_t N, int nchunk_max,
 #pragma unroll
     for (int k = 0; k < LP; ++k) acc[k] = 0.f;
     if (sl < 0) {
-      int c = 0;
-      for (; c + 2 <= nch; c += 2) {  // two chunks in flight
-        float q0[8], q1[8];
-        load8<T>(Qp + ((int64_t)c * N + i) * 8, q0);
-        load8<T>(Qp + ((int64_t)(c + 1) * N + i) * 8, q1);
+      for (int c = 0; c < nch; c += 4) {  // four chunks in flight
+        float q[4][8];
 #pragma unroll
-        for (int v = 0; v < 8; ++v)
+        for (int u = 0; u < 4; ++u) {
+          if (c + u < nch) {
+            load8<T>(Qp + ((int64_t)(c + u) * N + i) * 8, q[u]);
+          } else {
 #pragma unroll
-          for (int k = 0; k < LP; ++k) {
-            acc[k] = fmaf(q0[v], Cs[(c * 8 + v) * LP + k], acc[k]);
-            acc[k] = fmaf(q1[v], Cs[((c + 1) * 8 + v) * LP + k], acc[k]);
+            for (int v = 0; v < 8; ++v) q[u][v] = 0.f;
           }
-      }
-      if (c < nch) {
-        float q0[8];
-        load8<T>(Qp + ((int64_t)c * N + i) * 8, q0);
+        }
 #pragma unroll
-        for (int v = 0; v < 8; ++v)
+        for (int u = 0; u < 4; ++u)
 #pragma unroll
-          for (int k = 0; k < LP; ++k) acc[k] = fmaf(q0[v], Cs[(c * 8 + v) * LP + k], acc[k]);
+          for (int v = 0; v < 8; ++v)
+#pragma unroll
+            for (int k = 0; k < LP; ++k) acc[k] = fmaf(q[u][v], Cs[((c + u) * 8 + v) * LP + k], acc[k]);
       }
     }
     if (xhat) {
@@ -1550,6 +1703,7 @@ k_backproject_panel(const T* __restrict__ Qp, int64_t N, int nchunk_max,
         }
       }
       if (labels) labels[i] = (uint8_t)best;
+      if (clear_seedlab && sl >= 0) clear_seedlab[i] = -1;
     }
   }
 }
@@ -1568,7 +1722,7 @@ k_jacobi_step(const float* __restrict__ xin, float* __restrict__ xout,
               const float* __restrict__ s, int normalized, int kind, int ndim, int DX, int DY,
               int DZ, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colv,
               const float* __restrict__ ccsr, int64_t N, int L, float gamma, float omega,
-              int last, float* __restrict__ U, uint8_t* __restrict__ labels) {
+              int last, float* __restrict__ U, uint8_t* __restrict__ labels, int* clear_seedlab) {
   rw_grid_wait();
   rw_grid_trigger();
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -1633,26 +1787,110 @@ k_jacobi_step(const float* __restrict__ xin, float* __restrict__ xout,
     }
   }
   if (labels) labels[i] = (uint8_t)best;
+  if (clear_seedlab && sl >= 0) clear_seedlab[i] = -1;  // the label array is all -1 again for the next call
+}
+
+// The same damped-Jacobi step on a grid graph, launched as a 3-D grid (x in threads, y and z
+// in blocks) so a thread finds its voxel and its neighbours without integer division.
+template <int LP>
+__global__ void __launch_bounds__(128)
+k_jacobi_grid(const float* __restrict__ xin, float* __restrict__ xout,
+              const float* __restrict__ phat, const int* __restrict__ seedlab,
+              const float* __restrict__ cw, const float* __restrict__ d, const float* __restrict__ s,
+              int normalized, int ndim, int DX, int DY, int DZ, int64_t N, int L, float gamma,
+              float omega, int last, float* __restrict__ U, uint8_t* __restrict__ labels, int* clear_seedlab) {
+  rw_grid_wait();
+  rw_grid_trigger();
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= DX) return;
+  const int y = blockIdx.y, z = blockIdx.z;
+  const int64_t sy = DX, sz = (int64_t)DX * DY;
+  const int64_t i = x + sy * y + sz * z;
+  constexpr int NV = LP / 4;
+  const float4* xi4 = reinterpret_cast<const float4*>(xin);
+  float4 xv[NV];
+#pragma unroll
+  for (int t = 0; t < NV; ++t) xv[t] = xi4[i * NV + t];
+  const int sl = seedlab[i];
+  if (sl < 0) {
+    float4 acc[NV];
+#pragma unroll
+    for (int t = 0; t < NV; ++t) acc[t] = make_float4(0.f, 0.f, 0.f, 0.f);
+    auto add = [&](int64_t j, float c) {
+#pragma unroll
+      for (int t = 0; t < NV; ++t) {
+        const float4 v = xi4[j * NV + t];
+        acc[t].x = fmaf(c, v.x, acc[t].x); acc[t].y = fmaf(c, v.y, acc[t].y);
+        acc[t].z = fmaf(c, v.z, acc[t].z); acc[t].w = fmaf(c, v.w, acc[t].w);
+      }
+    };
+    if (x > 0) add(i - 1, cw[i - 1]);
+    if (x + 1 < DX) add(i + 1, cw[i]);
+    if (y > 0) add(i - sy, cw[N + i - sy]);
+    if (y + 1 < DY) add(i + sy, cw[N + i]);
+    if (ndim == 3) {
+      if (z > 0) add(i - sz, cw[2 * N + i - sz]);
+      if (z + 1 < DZ) add(i + sz, cw[2 * N + i]);
+    }
+    const float aii = (normalized ? 1.f : d[i]) + gamma;
+    const float f = omega / aii, keep = 1.f - omega;
+    const float4* p4 = reinterpret_cast<const float4*>(phat);
+#pragma unroll
+    for (int t = 0; t < NV; ++t) {
+      const float4 pv = p4[i * NV + t];
+      xv[t].x = keep * xv[t].x + f * fmaf(gamma, pv.x, acc[t].x);
+      xv[t].y = keep * xv[t].y + f * fmaf(gamma, pv.y, acc[t].y);
+      xv[t].z = keep * xv[t].z + f * fmaf(gamma, pv.z, acc[t].z);
+      xv[t].w = keep * xv[t].w + f * fmaf(gamma, pv.w, acc[t].w);
+    }
+  }
+  if (!last) {
+    float4* xo4 = reinterpret_cast<float4*>(xout);
+#pragma unroll
+    for (int t = 0; t < NV; ++t) xo4[i * NV + t] = xv[t];
+    return;
+  }
+  const float* xf = reinterpret_cast<const float*>(xv);
+  const float si = s[i];
+  int best = 0;
+  float bv = -INFINITY;
+#pragma unroll
+  for (int k = 0; k < LP; ++k) {
+    if (k < L) {
+      const float u = (sl >= 0) ? (k == sl ? 1.f : 0.f) : xf[k] * si;
+      U[i * L + k] = u;
+      if (u > bv) { bv = u; best = k; }
+    }
+  }
+  if (labels) labels[i] = (uint8_t)best;
+  if (clear_seedlab && sl >= 0) clear_seedlab[i] = -1;  // the label array is all -1 again for the next call
 }
 
 template <int LP>
 rw_status launch_jacobi(const rw_graph* g, const float* xin, float* xout, const float* phat,
                         const int* seedlab, int L, float gamma, float omega, int last,
-                        float* U, uint8_t* labels, cudaStream_t st) {
-  RW_LAUNCH((k_jacobi_step<LP>), rw_blocks(g->N, 256), 256, 0, st, 
+                        float* U, uint8_t* labels, int* clear, cudaStream_t st) {
+  if (g->kind == RW_GRAPH_GRID) {
+    const dim3 grid((unsigned)((g->dims[0] + 127) / 128), (unsigned)g->dims[1], (unsigned)g->dims[2]);
+    RW_LAUNCH((k_jacobi_grid<LP>), grid, 128, 0, st, xin, xout, phat, seedlab, g->cw, g->d, g->s,
+              g->normalized, g->ndim, g->dims[0], g->dims[1], g->dims[2], g->N, L, gamma, omega,
+              last, U, labels, clear);
+    return RW_OK;
+  }
+  RW_LAUNCH((k_jacobi_step<LP>), rw_blocks(g->N, 256), 256, 0, st,
       xin, xout, phat, seedlab, g->cw, g->d, g->s, g->normalized, g->kind, g->ndim, g->dims[0],
       g->dims[1], g->dims[2], g->rowptr, g->col, g->ccsr, g->N, L, gamma, omega, last, U,
-      labels);
+      labels, clear);
   return RW_OK;
 }
 
 rw_status jacobi(const rw_graph* g, int lp, const float* xin, float* xout, const float* phat,
                  const int* seedlab, int L, float gamma, float omega, int last, float* U,
-                 uint8_t* labels, cudaStream_t st) {
+                 uint8_t* labels, int* clear, cudaStream_t st) {
   switch (lp) {
-    case 4: return launch_jacobi<4>(g, xin, xout, phat, seedlab, L, gamma, omega, last, U, labels, st);
-    case 8: return launch_jacobi<8>(g, xin, xout, phat, seedlab, L, gamma, omega, last, U, labels, st);
-    default: return launch_jacobi<16>(g, xin, xout, phat, seedlab, L, gamma, omega, last, U, labels, st);
+    case 4: return launch_jacobi<4>(g, xin, xout, phat, seedlab, L, gamma, omega, last, U, labels, clear, st);
+    case 8: return launch_jacobi<8>(g, xin, xout, phat, seedlab, L, gamma, omega, last, U, labels, clear, st);
+    default: return launch_jacobi<16>(g, xin, xout, phat, seedlab, L, gamma, omega, last, U, labels, clear, st);
   }
 }
 
@@ -1660,20 +1898,22 @@ template <typename T, int LP>
 rw_status launch_proj_back(bool back, const T* Q, int ldq, const float* phat,
                            const int* seedlab, const rw_graph* g, const int* mdev, float* part,
                            int nblk, const float* C, float cscale, float* xhat, float* U,
-                           uint8_t* labels, int L, cudaStream_t st) {
+                           uint8_t* labels, int L, int* clear, cudaStream_t st) {
   constexpr int V = Vec16<T>::V;
   const int cpr = ldq / V;
   if constexpr (V == 8) {  // 16-bit copies: panel-major layout, ldq = 8 x chunks
     const int nchunk = ldq / 8;
     if (!back) {
-      const size_t shm = sizeof(float) * 8 * (size_t)nchunk * 8 * LP;
+      const size_t shm = sizeof(float) * kParts * (size_t)nchunk * 8 * LP;
       if (shm > 48 * 1024)
-        cudaFuncSetAttribute(k_project_panel<T, LP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
-      RW_LAUNCH((k_project_panel<T, LP>), nblk, 256, shm, st, Q, g->N, nchunk, phat, seedlab, mdev, part);
+        cudaFuncSetAttribute(k_project_cw<T, LP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+      const int64_t rpb = (g->N + nblk - 1) / nblk;
+      RW_LAUNCH((k_project_cw<T, LP>), nblk, 256, shm, st, Q, g->N, nchunk, phat, seedlab, mdev,
+                rpb, part);
     } else {
-      const size_t shm = sizeof(float) * (size_t)nchunk * 8 * LP;
+      const size_t shm = sizeof(float) * (size_t)((nchunk + 3) / 4 * 4) * 8 * LP;
       RW_LAUNCH((k_backproject_panel<T, LP>), nblk, 256, shm, st, Q, g->N, nchunk, C, cscale, seedlab,
-                                                        g->sq, g->s, L, mdev, xhat, U, labels);
+                                                        g->sq, g->s, L, mdev, xhat, U, labels, clear);
     }
     RW_LAUNCH_CHECK();
     return RW_OK;
@@ -1689,10 +1929,10 @@ rw_status launch_proj_back(bool back, const T* Q, int ldq, const float* phat,
   } else {
     if (cpr <= 32)
       RW_LAUNCH((k_backproject<T, LP, 1>), nblk, 256, 0, st, Q, ldq, cpr, C, cscale, seedlab, g->sq, g->s,
-                                                   g->N, L, mdev, xhat, U, labels);
+                                                   g->N, L, mdev, xhat, U, labels, clear);
     else if (cpr <= 64)
       RW_LAUNCH((k_backproject<T, LP, 2>), nblk, 256, 0, st, Q, ldq, cpr, C, cscale, seedlab, g->sq, g->s,
-                                                   g->N, L, mdev, xhat, U, labels);
+                                                   g->N, L, mdev, xhat, U, labels, clear);
     else
       return RW_ERR_UNSUPPORTED;
   }
@@ -1704,11 +1944,11 @@ rw_status launch_proj_back(bool back, const T* Q, int ldq, const float* phat,
 template <typename T>
 rw_status proj_back(int lp, bool back, const T* Q, int ldq, const float* phat, const int* seedlab,
                     const rw_graph* g, const int* mdev, float* part, int nblk, const float* C,
-                    float cscale, float* xhat, float* U, uint8_t* labels, int L, cudaStream_t st) {
+                    float cscale, float* xhat, float* U, uint8_t* labels, int L, cudaStream_t st, int* clear = nullptr) {
   switch (lp) {
-    case 4: return launch_proj_back<T, 4>(back, Q, ldq, phat, seedlab, g, mdev, part, nblk, C, cscale, xhat, U, labels, L, st);
-    case 8: return launch_proj_back<T, 8>(back, Q, ldq, phat, seedlab, g, mdev, part, nblk, C, cscale, xhat, U, labels, L, st);
-    default: return launch_proj_back<T, 16>(back, Q, ldq, phat, seedlab, g, mdev, part, nblk, C, cscale, xhat, U, labels, L, st);
+    case 4: return launch_proj_back<T, 4>(back, Q, ldq, phat, seedlab, g, mdev, part, nblk, C, cscale, xhat, U, labels, L, clear, st);
+    case 8: return launch_proj_back<T, 8>(back, Q, ldq, phat, seedlab, g, mdev, part, nblk, C, cscale, xhat, U, labels, L, clear, st);
+    default: return launch_proj_back<T, 16>(back, Q, ldq, phat, seedlab, g, mdev, part, nblk, C, cscale, xhat, U, labels, L, clear, st);
   }
 }
 
@@ -1761,21 +2001,33 @@ rw_status rw_solve_priors_internal(const rw_graph* g, const int32_t* seed_idx,
                                    int** seedlab_out, double** fit64_out) {
   rw_graph* gm = const_cast<rw_graph*>(g);
   SolveWorkspace& ws = gm->ws;
+  if (S > kMaxSeeds) return RW_ERR_INVALID_ARG;
+  const size_t cap0 = ws.seedlab.cap;
   RW_TRY(ws.seedlab.grow(sizeof(int) * g->N));
+  if (ws.seedlab.cap != cap0) ws.seeds_clean = false;
   RW_TRY(ws.phat.grow(sizeof(float) * g->N * lp));
-  // stats (48 doubles) + fit (48 floats) + fit64 (32 doubles) live in ws.pcg's head? use own buffer
-  static_assert(sizeof(double) * 48 + sizeof(float) * 48 + sizeof(double) * 32 < 2048, "");
-  if (gm->upd.cap < 4096) return RW_ERR_OOM;
-  double* stats = gm->upd.as<double>();
-  float* fit = reinterpret_cast<float*>(stats + 48);
-  double* fit64 = reinterpret_cast<double*>(fit + 48);
+  const int nsb = (S + 255) / 256;
+  const size_t need = 4096 + sizeof(float) * (size_t)nsb * 3 * L;
+  RW_TRY(ws.seedpart.grow(need));
+  float* bpart = reinterpret_cast<float*>(ws.seedpart.as<char>() + 4096);
+  double* fit64 = ws.seedpart.as<double>();
   int* seedlab = ws.seedlab.as<int>();
-  RW_LAUNCH(k_seed_reset, rw_blocks(g->N, 256), 256, 0, st, seedlab, g->N, stats, 48);
-  RW_LAUNCH(k_seed_scatter, rw_blocks(S, 256), 256, 0, st, seed_idx, seed_lab, S, L, g->N, g->J ? g->J : nullptr,
-                                                    seedlab, stats, g->status);
-  RW_LAUNCH(k_fit, 1, 32, 0, st, stats, L, prior_mode, fit, fit64, g->status);
-  RW_LAUNCH(k_priors, rw_blocks(g->N, 256), 256, 0, st, g->J, g->sq, g->N, L, lp, prior_mode, fit, priors,
-                                                 ws.phat.as<float>(), g->status);
+  // the labels array is all -1 between calls when the previous call's last kernel cleared its
+  // seeds (rw_solve does); otherwise reset it here
+  if (!ws.seeds_clean)
+    RW_LAUNCH(k_seed_reset, rw_blocks(g->N, 256), 256, 0, st, seedlab, g->N, nullptr, 0);
+  ws.seeds_clean = false;
+  RW_LAUNCH(k_seed_scatter, nsb, 256, 0, st, seed_idx, seed_lab, S, L, g->N,
+            g->J ? g->J : nullptr, seedlab, bpart, g->status);
+  if (lp == 4)
+    RW_LAUNCH(k_priors<4>, rw_blocks(g->N, 256), 256, 0, st, g->J, g->sq, g->N, L, prior_mode,
+              bpart, nsb, fit64, priors, ws.phat.as<float>(), g->status);
+  else if (lp == 8)
+    RW_LAUNCH(k_priors<8>, rw_blocks(g->N, 256), 256, 0, st, g->J, g->sq, g->N, L, prior_mode,
+              bpart, nsb, fit64, priors, ws.phat.as<float>(), g->status);
+  else
+    RW_LAUNCH(k_priors<16>, rw_blocks(g->N, 256), 256, 0, st, g->J, g->sq, g->N, L, prior_mode,
+              bpart, nsb, fit64, priors, ws.phat.as<float>(), g->status);
   *phat_out = ws.phat.as<float>();
   *seedlab_out = seedlab;
   if (fit64_out) *fit64_out = fit64;
@@ -1800,7 +2052,7 @@ static rw_status validate_solve(const rw_graph* g, const rw_basis* b, const int3
   if (mmax > kMaxSmallM) return RW_ERR_UNSUPPORTED;
   // one CTA holds an m x m FP32 matrix plus label-sized vectors in shared memory
   const size_t shm_adapt = sizeof(float) * ((size_t)mmax * (mmax | 1) + 3 * (size_t)L * mmax);
-  const size_t shm_small = sizeof(float) * ((size_t)mmax * (mmax | 1) + 3 * (size_t)L * mmax + mmax) +
+  const size_t shm_small = sizeof(float) * ((size_t)mmax * ((mmax + L) | 1) + 2 * (size_t)L * mmax + mmax) +
                            sizeof(int) * mmax;
   // + the kernels' static shared arrays (reciprocal diagonals, broadcast buffers, the
   // shifted copies of the LU panel's diagonal block)
@@ -1913,21 +2165,24 @@ extern "C" rw_status rw_solve(const rw_graph* g, const rw_basis* b, const int32_
     RW_LAUNCH_CHECK();
   }
   int ldq_e = fmt == RW_BASIS_F32 ? b->ld32 : b->ld16;
+  // projection blocks: the chunk-major 16-bit kernel takes 2 per SM (more rows per block, fewer
+  // partials to add); the FP32 row kernel 4 per SM
+  const int nblk_p = fmt == RW_BASIS_F32 ? nblk : 2 * sms;
   float zscale = fmt == RW_BASIS_F16 ? 1.f / b->qscale : 1.f;
   float cscale = fmt == RW_BASIS_F16 ? 1.f / b->qscale : 1.f;
   if (fmt == RW_BASIS_F16)
-    RW_TRY(proj_back<__half>(lp, false, b->Q16, ldq_e, phat, seedlab, g, mdev, part, nblk, nullptr, 0.f, nullptr, nullptr, nullptr, L, st));
+    RW_TRY(proj_back<__half>(lp, false, b->Q16, ldq_e, phat, seedlab, g, mdev, part, nblk_p, nullptr, 0.f, nullptr, nullptr, nullptr, L, st));
   else if (fmt == RW_BASIS_BF16)
-    RW_TRY(proj_back<__nv_bfloat16>(lp, false, b->Qbf, ldq_e, phat, seedlab, g, mdev, part, nblk, nullptr, 0.f, nullptr, nullptr, nullptr, L, st));
+    RW_TRY(proj_back<__nv_bfloat16>(lp, false, b->Qbf, ldq_e, phat, seedlab, g, mdev, part, nblk_p, nullptr, 0.f, nullptr, nullptr, nullptr, L, st));
   else
-    RW_TRY(proj_back<float>(lp, false, b->Q32, ldq_e, phat, seedlab, g, mdev, part, nblk, nullptr, 0.f, nullptr, nullptr, nullptr, L, st));
+    RW_TRY(proj_back<float>(lp, false, b->Q32, ldq_e, phat, seedlab, g, mdev, part, nblk_p, nullptr, 0.f, nullptr, nullptr, nullptr, L, st));
   RW_LAUNCH(k_reduce_partials, rw_blocks((int64_t)std::max(mq * lp, m_max) * 32, 256), 256, 0, st, 
-      part, nblk, ldq_e, lp, mq, zscale, Z, b->lam, gamma, m_max, lgam);
+      part, nblk_p, ldq_e, lp, mq, zscale, Z, b->lam, gamma, m_max, lgam);
   RW_TRY(mark(4));
   // small system
   float* C = reinterpret_cast<float*>(P(lay.C));
   {
-    size_t shm = sizeof(float) * ((size_t)m_max * (m_max | 1) + 3 * (size_t)L * m_max + m_max) +
+    size_t shm = sizeof(float) * ((size_t)m_max * ((m_max + L) | 1) + 2 * (size_t)L * m_max + m_max) +
                  sizeof(int) * m_max;
     if (lp == 4) {
       cudaFuncSetAttribute(k_small_solve<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
@@ -1956,11 +2211,11 @@ extern "C" rw_status rw_solve(const rw_graph* g, const rw_basis* b, const int32_
     xh1 = ws.xhat[1].as<float>();
   }
   if (fmt == RW_BASIS_F16)
-    RW_TRY(proj_back<__half>(lp, true, b->Q16, ldq_e, phat, seedlab, g, mdev, part, nblk, C, cscale, xh0, prob_dev, labels_dev, L, st));
+    RW_TRY(proj_back<__half>(lp, true, b->Q16, ldq_e, phat, seedlab, g, mdev, part, nblk, C, cscale, xh0, prob_dev, labels_dev, L, st, steps == 0 ? seedlab : nullptr));
   else if (fmt == RW_BASIS_BF16)
-    RW_TRY(proj_back<__nv_bfloat16>(lp, true, b->Qbf, ldq_e, phat, seedlab, g, mdev, part, nblk, C, cscale, xh0, prob_dev, labels_dev, L, st));
+    RW_TRY(proj_back<__nv_bfloat16>(lp, true, b->Qbf, ldq_e, phat, seedlab, g, mdev, part, nblk, C, cscale, xh0, prob_dev, labels_dev, L, st, steps == 0 ? seedlab : nullptr));
   else
-    RW_TRY(proj_back<float>(lp, true, b->Q32, ldq_e, phat, seedlab, g, mdev, part, nblk, C, cscale, xh0, prob_dev, labels_dev, L, st));
+    RW_TRY(proj_back<float>(lp, true, b->Q32, ldq_e, phat, seedlab, g, mdev, part, nblk, C, cscale, xh0, prob_dev, labels_dev, L, st, steps == 0 ? seedlab : nullptr));
   RW_TRY(mark(6));
   if (steps > 0) {
     if (opts->refine_mode == RW_REFINE_JACOBI) {
@@ -1969,7 +2224,8 @@ extern "C" rw_status rw_solve(const rw_graph* g, const rw_basis* b, const int32_
       for (int t = 0; t < steps; ++t) {
         int last = (t == steps - 1);
         RW_TRY(jacobi(g, lp, a, c, phat, seedlab, L, (float)gamma, omega, last,
-                      last ? prob_dev : nullptr, last ? labels_dev : nullptr, st));
+                      last ? prob_dev : nullptr, last ? labels_dev : nullptr,
+                      last ? seedlab : nullptr, st));
         std::swap(a, c);
       }
     } else {
@@ -1977,6 +2233,9 @@ extern "C" rw_status rw_solve(const rw_graph* g, const rw_basis* b, const int32_
                          nullptr, st));
     }
   }
+  // the final kernel (last Jacobi step, or the back-projection without refinement) cleared the
+  // seeds from the label array
+  if (steps == 0 || opts->refine_mode == RW_REFINE_JACOBI) ws.seeds_clean = true;
   RW_TRY(mark(7));
   if (info) {
     RW_TRY(ws.host.grow(4096));

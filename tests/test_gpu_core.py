@@ -290,3 +290,66 @@ def test_pcg_fixed_iterations_match_oracle_recurrence(c1):
         assert np.abs(prob.cpu().numpy() - U).max() <= 1e-4
     finally:
         rw.rw_graph_free(g)
+
+
+def test_consecutive_solves_on_one_graph(c1):
+    """The seed labels of one call must not leak into the next: a sequence of solves on the same
+    handles (different seed sets, refinement by Jacobi, by PCG and none, a PCG solve and a
+    failing call with a duplicated seed in between) matches fresh solves of each seed set."""
+    J, dims, truth = c1["J"], c1["dims"], c1["truth"]
+    sets = [synth.sample_seeds(truth, dims, 20, 2, seed=synth.BASE_SEED + 300 + k) for k in range(4)]
+    g = rw.rw_build_graph(to_dev(J, torch.float32), dims, c1["beta"])
+    b = rw.rw_basis_create(g, to_dev(c1["Q"], torch.float32), c1["lam"])
+    N = c1["g"].N
+    prob = torch.empty(N, 2, device=dev())
+    lab = torch.empty(N, dtype=torch.uint8, device=dev())
+    plan = [(0, 3, rw.RW_REFINE_JACOBI), (1, 0, rw.RW_REFINE_JACOBI), (2, 4, rw.RW_REFINE_PCG),
+            (3, 3, rw.RW_REFINE_JACOBI), (0, 3, rw.RW_REFINE_JACOBI)]
+    try:
+        for step, (k, steps, mode) in enumerate(plan):
+            si, sl = sets[k]
+            if step == 2:   # a basic-RW solve and a failing call in between
+                rw.rw_solve_pcg(g, to_dev(sets[1][0]), to_dev(sets[1][1]), 2, prob, iters=5)
+                dup_i = np.concatenate([sets[3][0], sets[3][0][:1]]).astype(np.int32)
+                dup_l = np.concatenate([sets[3][1], sets[3][1][:1]]).astype(np.int32)
+                with pytest.raises(rw.RWError):
+                    rw.rw_solve(g, b, to_dev(dup_i), to_dev(dup_l), 2, prob, lab, m=30,
+                                refine_steps=3)
+            rw.rw_solve(g, b, to_dev(si), to_dev(sl), 2, prob, lab, m=30, refine_steps=steps,
+                        refine_mode=mode)
+            U = prob.cpu().numpy().astype(np.float64)
+            ref = pipeline.online_solve(c1["g"], c1["Q"], c1["lam"], si, sl, 2, gamma=1e-3, m=30,
+                                        refine_steps=steps,
+                                        refine_method="pcg" if mode == rw.RW_REFINE_PCG else "jacobi")
+            tol = 5e-3 if mode == rw.RW_REFINE_PCG else TOL_PROB  # PCG amplifies start differences
+            assert np.abs(U - ref["U"]).max() <= tol, (step, np.abs(U - ref["U"]).max())
+            onehot = np.eye(2)[sl]
+            np.testing.assert_array_equal(U[si], onehot)
+    finally:
+        rw.rw_basis_free(b)
+        rw.rw_graph_free(g)
+
+
+def test_zero_pivot_takes_the_pivoting_path(c1):
+    """Basis values chosen so that the Woodbury matrix diag(lambda + gamma) - Q_s^T X has a zero
+    first diagonal entry: the unpivoted LU must detect it and the partial-pivoting path must
+    still match the oracle's S x S solve of Eq. (Fs)."""
+    m, gamma = 12, 1e-3
+    Q = c1["Q"][:, :m]
+    lam = c1["lam"][:m].copy()
+    P = f32(priors.gaussian_priors(c1["J"], c1["si"], c1["sl"], 2))
+    _, parts = fastrw.fast_rw(c1["g"], Q, lam, c1["si"], c1["sl"], 2, P, gamma, return_parts=True)
+    K = Q[c1["si"]].T @ parts["X"]
+    lam[0] = float(np.float32(K[0, 0])) - gamma   # M_00 = lambda_0 + gamma - K_00 = 0
+    ref = fastrw.fast_rw(c1["g"], Q, lam, c1["si"], c1["sl"], 2, P, gamma)
+    g = rw.rw_build_graph(to_dev(c1["J"], torch.float32), c1["dims"], c1["beta"])
+    b = rw.rw_basis_create(g, to_dev(np.ascontiguousarray(Q), torch.float32), lam)
+    try:
+        prob = torch.empty(c1["g"].N, 2, device=dev())
+        rw.rw_solve(g, b, to_dev(c1["si"]), to_dev(c1["sl"]), 2, prob, priors=to_dev(P, torch.float32),
+                    prior_mode=1, gamma=gamma, m=m, refine_steps=0, basis_format=rw.RW_BASIS_F32)
+        err = np.abs(prob.cpu().numpy() - ref).max()
+        assert err <= 1e-3, err
+    finally:
+        rw.rw_basis_free(b)
+        rw.rw_graph_free(g)
