@@ -235,31 +235,62 @@ __global__ void k_seed_gather(const int32_t* __restrict__ idx, const int32_t* __
     if (lane < lp) { Us[lane] = 0.f; R0[lane] = 0.f; }
     return;
   }
+  // X row = -sum over unseeded neighbours j of c_ij q_j, kept in registers (mp <= 224)
   const float* qi = Q + (int64_t)i * ldq;
-  for (int c = lane; c < mp; c += 32) { qs[c] = qi[c]; xs[c] = 0.f; }
+  float acc[7], own[7];
+#pragma unroll
+  for (int q = 0; q < 7; ++q) {
+    const int c = lane + 32 * q;
+    own[q] = c < mp ? qi[c] : 0.f;
+    acc[q] = 0.f;
+  }
   float r0 = 0.f;  // lane k accumulates column k of L-hat_s U-hat_s
   const float diag = normalized ? 1.f : d[i];
   if (lane == k0) r0 = diag * sq[i];
-  auto visit = [&](int64_t j, float c) {
-    int lj = seedlab[j];
+  auto visit = [&](int64_t j, float c, int lj) {
     if (lj < 0) {
       const float* qj = Q + j * ldq;
-      for (int cc = lane; cc < mp; cc += 32) xs[cc] = fmaf(-c, qj[cc], xs[cc]);
+#pragma unroll
+      for (int q = 0; q < 7; ++q) {
+        const int cc = lane + 32 * q;
+        if (cc < mp) acc[q] = fmaf(-c, qj[cc], acc[q]);
+      }
     } else if (lane == lj) {
       r0 -= c * sq[j];
     }
   };
   if (kind == RW_GRAPH_GRID) {
+    // all neighbours' indices, coefficients and labels first (independent loads)
+    const int x = i % DX, y = (i / DX) % DY, z = i / (DX * DY);
     const int64_t st[3] = {1, (int64_t)DX, (int64_t)DX * DY};
-    const int cc[3] = {(int)(i % DX), (int)((i / DX) % DY), (int)(i / ((int64_t)DX * DY))};
-    const int n[3] = {DX, DY, DZ};
-    for (int a = 0; a < ndim; ++a) {
-      if (cc[a] > 0) visit(i - st[a], cw[a * N + i - st[a]]);
-      if (cc[a] + 1 < n[a]) visit(i + st[a], cw[a * N + i]);
+    const int cc3[3] = {x, y, z};
+    const int n3[3] = {DX, DY, DZ};
+    int64_t nj[6];
+    float nc[6];
+    int nl[6];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const bool lo = a < ndim && cc3[a] > 0, hi = a < ndim && cc3[a] + 1 < n3[a];
+      nj[2 * a] = lo ? i - st[a] : -1;
+      nj[2 * a + 1] = hi ? i + st[a] : -1;
+      nc[2 * a] = lo ? cw[a * N + i - st[a]] : 0.f;
+      nc[2 * a + 1] = hi ? cw[a * N + i] : 0.f;
     }
+#pragma unroll
+    for (int u = 0; u < 6; ++u) nl[u] = nj[u] >= 0 ? seedlab[nj[u]] : -2;
+#pragma unroll
+    for (int u = 0; u < 6; ++u)
+      if (nj[u] >= 0) visit(nj[u], nc[u], nl[u]);
   } else {
-    for (int p = rowptr[i]; p < rowptr[i + 1]; ++p) visit(colv[p], ccsr[p]);
+    for (int p = rowptr[i]; p < rowptr[i + 1]; ++p) visit(colv[p], ccsr[p], seedlab[colv[p]]);
   }
+#pragma unroll
+  for (int q = 0; q < 7; ++q) {
+    const int c = lane + 32 * q;
+    if (c < mp) { qs[c] = own[q]; xs[c] = acc[q]; }
+  }
+  // a fixed-m solve on a wider basis: the columns past 224 are never read (m <= 224)
+  for (int c = 224 + lane; c < mp; c += 32) { qs[c] = 0.f; xs[c] = 0.f; }
   if (lane < lp) {
     float u = (lane == k0) ? sq[i] : 0.f;
     Us[lane] = u;
@@ -673,7 +704,7 @@ __device__ void seed_residuals(const float* __restrict__ Qs, int ldq, const floa
 // through distributed shared memory, so the sums have a fixed order.  (S is a few thousand at
 // most, so FP32 partial sums over S / cluster rows are accurate to a few ulps of the result.)
 // ---------------------------------------------------------------------------------------
-constexpr int kSgT = 64, kSgK = 32, kSgMaxCluster = 8;
+constexpr int kSgT = 64, kSgRows = 128, kSgMaxCluster = 8;
 
 __global__ void __launch_bounds__(256)
 k_seed_gram(const float* __restrict__ A, int lda, const float* __restrict__ B, int ldb, int S,
@@ -681,29 +712,35 @@ k_seed_gram(const float* __restrict__ A, int lda, const float* __restrict__ B, i
   rw_grid_wait();
   rw_grid_trigger();
   cg::cluster_group cluster = cg::this_cluster();
-  __shared__ float As[kSgK][kSgT + 4];
-  __shared__ float Bs[kSgK][kSgT + 4];
+  extern __shared__ float4 stage4[];          // As[kSgRows][17] | Bs[kSgRows][17] (float4)
   __shared__ float4 part[kSgT * kSgT / 4];
+  float4* As = stage4;
+  float4* Bs = stage4 + kSgRows * 17;
   const int i0 = blockIdx.x * kSgT, j0 = blockIdx.y * kSgT;
   const int nz = gridDim.z, rank = (int)cluster.block_rank();
-  const int rpc = ((S + nz - 1) / nz + kSgK - 1) / kSgK * kSgK;
+  const int rpc = (S + nz - 1) / nz;
   const int r0 = rank * rpc, r1 = min(S, r0 + rpc);
   const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
   float acc[4][4] = {};
-  for (int k0 = r0; k0 < r1; k0 += kSgK) {
-    for (int e = threadIdx.x; e < kSgK * kSgT; e += 256) {
-      const int kk = e / kSgT, ii = e % kSgT;
+  for (int k0 = r0; k0 < r1; k0 += kSgRows) {
+    // the whole stage (kSgRows rows of the two 64-column tiles) in flight before one barrier
+    for (int e = threadIdx.x; e < kSgRows * 16; e += 256) {
+      const int kk = e / 16, c4 = e % 16;
       const int r = k0 + kk;
       const bool rin = r < r1;
-      As[kk][ii] = (rin && i0 + ii < p) ? A[(int64_t)r * lda + i0 + ii] : 0.f;
-      Bs[kk][ii] = (rin && j0 + ii < q) ? B[(int64_t)r * ldb + j0 + ii] : 0.f;
+      As[kk * 17 + c4] = (rin && i0 + 4 * c4 < p)
+          ? __ldg(reinterpret_cast<const float4*>(A + (int64_t)r * lda + i0) + c4)
+          : make_float4(0.f, 0.f, 0.f, 0.f);
+      Bs[kk * 17 + c4] = (rin && j0 + 4 * c4 < q)
+          ? __ldg(reinterpret_cast<const float4*>(B + (int64_t)r * ldb + j0) + c4)
+          : make_float4(0.f, 0.f, 0.f, 0.f);
     }
     __syncthreads();
-#pragma unroll 8
-    for (int kk = 0; kk < kSgK; ++kk) {
-      float a[4], b[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) { a[u] = As[kk][ty * 4 + u]; b[u] = Bs[kk][tx * 4 + u]; }
+    const int kn = min(kSgRows, r1 - k0);
+#pragma unroll 4
+    for (int kk = 0; kk < kn; ++kk) {
+      const float4 av = As[kk * 17 + ty], bv = Bs[kk * 17 + tx];
+      const float a[4] = {av.x, av.y, av.z, av.w}, b[4] = {bv.x, bv.y, bv.z, bv.w};
 #pragma unroll
       for (int u = 0; u < 4; ++u)
 #pragma unroll
@@ -1972,11 +2009,14 @@ rw_status rw_solve_priors_internal(const rw_graph* g, const int32_t* seed_idx,
 // launches k_seed_gram with the seed rows split over a cluster of up to 8 CTAs along z
 static rw_status seed_gram(const float* A, int lda, const float* B, int ldb, int S, int p, int q,
                            float* G, int ldg, cudaStream_t st) {
-  const int nz = std::max(1, std::min(kSgMaxCluster, (S + 191) / 192));
+  // enough CTAs along z that each holds at most one stage of rows (up to the cluster limit)
+  const int nz = std::max(1, std::min(kSgMaxCluster, (S + kSgRows - 1) / kSgRows));
+  const size_t shm = sizeof(float4) * 2 * kSgRows * 17;
+  RW_CHECK_CUDA(cudaFuncSetAttribute(k_seed_gram, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((p + kSgT - 1) / kSgT, (q + kSgT - 1) / kSgT, nz);
   cfg.blockDim = dim3(256, 1, 1);
-  cfg.dynamicSmemBytes = 0;
+  cfg.dynamicSmemBytes = shm;
   cfg.stream = st;
   cudaLaunchAttribute attr[2];
   attr[0].id = cudaLaunchAttributeClusterDimension;
