@@ -205,10 +205,10 @@ def phase_work(phase, N, m, lp, S, L, steps):
     raise KeyError(phase)
 
 
-PHASE_KERNELS = {"seeds": "k_fill_i32+k_seed_scatter+k_fit+k_priors",
-                 "gather": "k_seed_gather+k_gram", "adapt": "k_adapt",
-                 "project": "k_project_panel+k_reduce_partials", "small": "k_small_solve",
-                 "back": "k_backproject_panel", "refine": "k_jacobi_step x3"}
+PHASE_KERNELS = {"seeds": "k_seed_scatter+k_priors",
+                 "gather": "k_seed_gather+k_seed_gram", "adapt": "k_adapt",
+                 "project": "k_project_cw+k_reduce_partials", "small": "k_small_solve",
+                 "back": "k_backproject_panel", "refine": "k_jacobi_grid x3"}
 
 
 def rooflines(phases, N, m, lp, S, L, steps, hbm, sm_mhz):

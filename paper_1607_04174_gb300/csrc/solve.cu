@@ -176,39 +176,41 @@ k_priors(const float* __restrict__ J, const float* __restrict__ sq, int64_t N, i
   else if (blockIdx.x == 0)
     seed_fit(bpart, nsb, L, prior_mode, fit, fit64, nullptr);
   __syncthreads();
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= N) return;
-  float p[LP];
-  if (prior_mode == 0) {
-    const float x = J[i];
-    float mx = -INFINITY;
+  // grid-stride over the voxels (a few waves of blocks, so the fit above is amortized)
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    float p[LP];
+    if (prior_mode == 0) {
+      const float x = J[i];
+      float mx = -INFINITY;
 #pragma unroll
-    for (int k = 0; k < LP; ++k) {
-      const float t = x - fit[k];
-      p[k] = (k < L) ? -t * t * fit[16 + k] - fit[32 + k] : -INFINITY;
-      mx = fmaxf(mx, p[k]);
+      for (int k = 0; k < LP; ++k) {
+        const float t = x - fit[k];
+        p[k] = (k < L) ? -t * t * fit[16 + k] - fit[32 + k] : -INFINITY;
+        mx = fmaxf(mx, p[k]);
+      }
+      float sum = 0.f;
+#pragma unroll
+      for (int k = 0; k < LP; ++k) {
+        p[k] = (k < L) ? __expf(p[k] - mx) : 0.f;
+        sum += p[k];
+      }
+      const float inv = 1.f / sum;
+#pragma unroll
+      for (int k = 0; k < LP; ++k) p[k] *= inv;
+    } else {
+#pragma unroll
+      for (int k = 0; k < LP; ++k) {
+        p[k] = (k < L) ? Pin[i * L + k] : 0.f;
+        if (k < L && !isfinite(p[k])) atomicOr(status, RW_DEV_NONFINITE);
+      }
     }
-    float sum = 0.f;
+    const float r = sq[i];
+    float4* o = reinterpret_cast<float4*>(phat + i * LP);
 #pragma unroll
-    for (int k = 0; k < LP; ++k) {
-      p[k] = (k < L) ? __expf(p[k] - mx) : 0.f;
-      sum += p[k];
-    }
-    const float inv = 1.f / sum;
-#pragma unroll
-    for (int k = 0; k < LP; ++k) p[k] *= inv;
-  } else {
-#pragma unroll
-    for (int k = 0; k < LP; ++k) {
-      p[k] = (k < L) ? Pin[i * L + k] : 0.f;
-      if (k < L && !isfinite(p[k])) atomicOr(status, RW_DEV_NONFINITE);
-    }
+    for (int k4 = 0; k4 < LP / 4; ++k4)
+      o[k4] = make_float4(r * p[4 * k4], r * p[4 * k4 + 1], r * p[4 * k4 + 2], r * p[4 * k4 + 3]);
   }
-  const float r = sq[i];
-  float4* o = reinterpret_cast<float4*>(phat + i * LP);
-#pragma unroll
-  for (int k4 = 0; k4 < LP / 4; ++k4)
-    o[k4] = make_float4(r * p[4 * k4], r * p[4 * k4 + 1], r * p[4 * k4 + 2], r * p[4 * k4 + 3]);
 }
 
 // One warp per seed: Q_s row, X = B-hat Q_n row, U-hat_s row, r0 = L-hat_s U-hat_s + g U-hat_s
@@ -379,7 +381,9 @@ __device__ __forceinline__ void shift_update(float (&a)[32], float f, const floa
 
 // Cholesky of the kb x kb diagonal block at (k0, k0), kb <= 32, by one warp.  buf: 128 floats,
 // 16-byte aligned (two halves: the column below the pivot at [0, 32), the pivot at [32]).
-// On return the block holds L (lower, diagonal included) and dinv[0..kb) = 1 / L_cc.
+// Every lane forms 1 / sqrt(pivot) beside the elimination (it only feeds the stores), so the
+// entries of L are written final at their step.  On return the block holds L (lower, diagonal
+// included) and dinv[0..kb) = 1 / L_cc.
 __device__ void chol_diag_rot(float* A, int ms, int k0, int kb, float* dinv, float* buf, int* bad) {
   const int lane = threadIdx.x & 31;
   const bool live = lane < kb;
@@ -391,27 +395,24 @@ __device__ void chol_diag_rot(float* A, int ms, int k0, int kb, float* dinv, flo
     if (live && c <= lane) v = row[c];
     a[c] = v;
   }
-  float dmine = 1.f;
   for (int kk = 0; kk < kb; ++kk) {
     float* b = buf + 64 * (kk & 1);
     if (lane > kk) b[lane - kk - 1] = a[0];  // a_lane,kk below the pivot
     else if (lane == kk) b[32] = a[0];       // pivot
     __syncwarp();
     float d = b[32];
-    if (lane == kk) dmine = d;
-    if (!(d > 0.f)) d = 1e-30f;
+    if (!(d > 0.f)) {
+      if (lane == kk) *bad = 1;
+      d = 1e-30f;
+    }
     const float f = __fdividef(a[0], d);
-    if (live && lane > kk) row[kk] = a[0];   // unscaled L entry (l_rk d_k)
+    const float ri = rsqrtf(d);
+    if (live && lane > kk) row[kk] = a[0] * ri;  // L_lane,kk
+    if (lane == kk) {
+      row[kk] = d * ri;                          // L_kk = sqrt(d)
+      dinv[kk] = ri;
+    }
     shift_update(a, f, b);
-  }
-  if (live && !(dmine > 0.f)) { *bad = 1; dmine = 1e-30f; }
-  const float di = rsqrtf(dmine);
-  __syncwarp();
-  if (live) dinv[lane] = di;
-  __syncwarp();
-  if (live) {
-    for (int c = 0; c < lane; ++c) row[c] *= dinv[c];
-    row[lane] = 1.f / di;
   }
   __syncwarp();
 }
@@ -1500,82 +1501,6 @@ k_backproject(const T* __restrict__ Q, int ldq, int cpr, const float* __restrict
 template <typename T>
 __device__ __forceinline__ void load8(const T* p, float* o) { Vec16<T>::load(p, o); }
 
-// Z = Q_n^T P-hat_n on the panel layout: lane = row (32 consecutive rows per warp step), the
-// 8 x LP products of one chunk are reduced across the warp by a reduce-scatter butterfly and
-// accumulated per warp in shared memory; warps are summed in a fixed order into per-block
-// partials.
-template <typename T, int LP>
-__global__ void __launch_bounds__(256)
-k_project_panel(const T* __restrict__ Qp, int64_t N, int nchunk_max,
-                const float* __restrict__ phat, const int* __restrict__ seedlab,
-                const int* __restrict__ mdev, float* __restrict__ part) {
-  rw_grid_wait();
-  rw_grid_trigger();
-  constexpr int NV = 8 * LP;       // products per row and chunk
-  constexpr int NG = NV / 32;      // groups of 32 reduced at once
-  extern __shared__ float red[];   // nw x (nchunk_max * NV)
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const int m = mdev[0];
-  const int nch = min((m + 7) / 8, nchunk_max);
-  float* wred = red + (size_t)warp * nchunk_max * NV;
-  for (int e = lane; e < nchunk_max * NV; e += 32) wred[e] = 0.f;
-  __syncwarp();
-  const int64_t ngrp = (N + 31) / 32;
-  for (int64_t gI = (int64_t)blockIdx.x * nw + warp; gI < ngrp; gI += (int64_t)gridDim.x * nw) {
-    const int64_t i = gI * 32 + lane;
-    float p[LP];
-    bool use = false;
-    if (i < N) use = __ldg(seedlab + i) < 0;
-    if (use) {
-#pragma unroll
-      for (int k4 = 0; k4 < LP / 4; ++k4) {
-        float4 pv = __ldg(reinterpret_cast<const float4*>(phat + i * LP) + k4);
-        p[4 * k4] = pv.x; p[4 * k4 + 1] = pv.y; p[4 * k4 + 2] = pv.z; p[4 * k4 + 3] = pv.w;
-      }
-    } else {
-#pragma unroll
-      for (int k = 0; k < LP; ++k) p[k] = 0.f;
-    }
-    for (int c = 0; c < nch; ++c) {
-      float q[8];
-      if (use) {
-        load8<T>(Qp + ((int64_t)c * N + i) * 8, q);
-      } else {
-#pragma unroll
-        for (int v = 0; v < 8; ++v) q[v] = 0.f;
-      }
-#pragma unroll
-      for (int gq = 0; gq < NG; ++gq) {
-        float val[32];
-#pragma unroll
-        for (int t = 0; t < 32; ++t) {
-          const int j = gq * 32 + t;
-          val[t] = q[j / LP] * p[j % LP];
-        }
-#pragma unroll
-        for (int half = 16, off = 16; half >= 1; half >>= 1, off >>= 1) {
-          const bool up = (lane & off) != 0;
-#pragma unroll
-          for (int t = 0; t < half; ++t) {
-            const float send = up ? val[t] : val[t + half];
-            const float keep = up ? val[t + half] : val[t];
-            val[t] = keep + __shfl_xor_sync(0xffffffff, send, off);
-          }
-        }
-        wred[c * NV + gq * 32 + lane] += val[0];  // lane holds product index gq*32 + lane
-      }
-    }
-  }
-  __syncthreads();
-  // block partial: sum the warps in order; entry (col = 8c + v, k) at col * LP + k
-  for (int e = threadIdx.x; e < nchunk_max * NV; e += blockDim.x) {
-    float s = 0.f;
-    for (int w = 0; w < nw; ++w) s += red[(size_t)w * nchunk_max * NV + e];
-    // e = c * NV + j, j = v * LP + k  ->  (8c + v) * LP + k = e
-    part[(int64_t)blockIdx.x * nchunk_max * NV + e] = s;
-  }
-}
-
 // Z partials on the panel layout, chunk-major: a block owns a range of rows, split into
 // kParts parts; warps take (chunk, part) items, a lane walks the item's rows (8 rows of 16 bytes
 // in flight per lane) and keeps the 8 x LPG products of one label group in registers; a single
@@ -1625,25 +1550,28 @@ k_project_cw(const T* __restrict__ Qp, int64_t N, int nchunk_max, const float* _
     for (int64_t i0 = a0 + lane; i0 < a1; i0 += 32 * 8) {
       uint4 raw[8];            // 8 rows of this chunk in flight, converted at use
       float p[8][LPG];
+      // the basis row, the prior row and the seed flag are loaded together (one round trip);
+      // seed rows are masked afterwards
+      int sl[8];
 #pragma unroll
       for (int u = 0; u < 8; ++u) {
         const int64_t i = i0 + 32 * u;
-        bool use = i < a1;
-        if (use) use = __ldg(seedlab + i) < 0;
-        raw[u] = use ? __ldg(reinterpret_cast<const uint4*>(qc + i * 8)) : make_uint4(0, 0, 0, 0);
-        if (use) {
-          if constexpr (LPG == 4) {
-            const float4 pv = __ldg(reinterpret_cast<const float4*>(phat + i * LP + g * LPG));
-            p[u][0] = pv.x; p[u][1] = pv.y; p[u][2] = pv.z; p[u][3] = pv.w;
-          } else {
-#pragma unroll
-            for (int k = 0; k < LPG; ++k) p[u][k] = __ldg(phat + i * LP + g * LPG + k);
-          }
+        const bool inb = i < a1;
+        sl[u] = inb ? __ldg(seedlab + i) : 0;
+        raw[u] = inb ? __ldg(reinterpret_cast<const uint4*>(qc + i * 8)) : make_uint4(0, 0, 0, 0);
+        if constexpr (LPG == 4) {
+          const float4 pv = inb ? __ldg(reinterpret_cast<const float4*>(phat + i * LP + g * LPG))
+                                : make_float4(0.f, 0.f, 0.f, 0.f);
+          p[u][0] = pv.x; p[u][1] = pv.y; p[u][2] = pv.z; p[u][3] = pv.w;
         } else {
 #pragma unroll
-          for (int k = 0; k < LPG; ++k) p[u][k] = 0.f;
+          for (int k = 0; k < LPG; ++k) p[u][k] = inb ? __ldg(phat + i * LP + g * LPG + k) : 0.f;
         }
       }
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+#pragma unroll
+        for (int k = 0; k < LPG; ++k) p[u][k] = sl[u] < 0 ? p[u][k] : 0.f;
 #pragma unroll
       for (int u = 0; u < 8; ++u) {
         float q[8];
@@ -1673,6 +1601,8 @@ k_project_cw(const T* __restrict__ Qp, int64_t N, int nchunk_max, const float* _
 
 // U-hat_n = Q_n C on the panel layout: lane = row, the chunk's 8 x LP coefficients come from
 // shared memory as broadcasts; no cross-lane reduction.
+constexpr int kBackChunks = 8;  // 16-byte chunks per row in flight in the back-projection
+
 template <typename T, int LP>
 __global__ void __launch_bounds__(256)
 k_backproject_panel(const T* __restrict__ Qp, int64_t N, int nchunk_max,
@@ -1682,38 +1612,50 @@ k_backproject_panel(const T* __restrict__ Qp, int64_t N, int nchunk_max,
                     float* __restrict__ U, uint8_t* __restrict__ labels, int* clear_seedlab) {
   rw_grid_wait();
   rw_grid_trigger();
-  extern __shared__ float Cs[];  // (8 nchunk_max, rounded up to 4 chunks) x LP
+  extern __shared__ float Cs[];  // (8 nchunk_max, rounded up to kBackChunks chunks) x LP
   const int m = mdev[0];
   const int nch = min((m + 7) / 8, nchunk_max);
-  const int ncs = (nchunk_max + 3) / 4 * 4;
+  const int ncs = (nchunk_max + kBackChunks - 1) / kBackChunks * kBackChunks;
   for (int e = threadIdx.x; e < ncs * 8 * LP; e += blockDim.x)
     Cs[e] = e < nchunk_max * 8 * LP ? Cg[e] * cscale : 0.f;
   __syncthreads();
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
        i += (int64_t)gridDim.x * blockDim.x) {
+    // the seed flag and the first chunks are loaded together (one round trip); seed rows
+    // discard the products
     const int sl = __ldg(seedlab + i);
     float acc[LP];
 #pragma unroll
     for (int k = 0; k < LP; ++k) acc[k] = 0.f;
-    if (sl < 0) {
-      for (int c = 0; c < nch; c += 4) {  // four chunks in flight
-        float q[4][8];
+    for (int c = 0; c < nch; c += kBackChunks) {  // kBackChunks chunks in flight
+      uint4 raw[kBackChunks];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          if (c + u < nch) {
-            load8<T>(Qp + ((int64_t)(c + u) * N + i) * 8, q[u]);
-          } else {
+      for (int u = 0; u < kBackChunks; ++u)
+        raw[u] = c + u < nch ? __ldg(reinterpret_cast<const uint4*>(Qp + ((int64_t)(c + u) * N + i) * 8))
+                             : make_uint4(0, 0, 0, 0);
 #pragma unroll
-            for (int v = 0; v < 8; ++v) q[u][v] = 0.f;
+      for (int u = 0; u < kBackChunks; ++u) {
+        if (c + u < nch) {  // uniform over the block
+          float q[8];
+          Vec16<T>::unpack(raw[u], q);
+#pragma unroll
+          for (int v = 0; v < 8; ++v) {
+            const float4* cr = reinterpret_cast<const float4*>(Cs + ((c + u) * 8 + v) * LP);
+#pragma unroll
+            for (int k4 = 0; k4 < LP / 4; ++k4) {
+              const float4 cv = cr[k4];
+              acc[4 * k4 + 0] = fmaf(q[v], cv.x, acc[4 * k4 + 0]);
+              acc[4 * k4 + 1] = fmaf(q[v], cv.y, acc[4 * k4 + 1]);
+              acc[4 * k4 + 2] = fmaf(q[v], cv.z, acc[4 * k4 + 2]);
+              acc[4 * k4 + 3] = fmaf(q[v], cv.w, acc[4 * k4 + 3]);
+            }
           }
         }
-#pragma unroll
-        for (int u = 0; u < 4; ++u)
-#pragma unroll
-          for (int v = 0; v < 8; ++v)
-#pragma unroll
-            for (int k = 0; k < LP; ++k) acc[k] = fmaf(q[u][v], Cs[((c + u) * 8 + v) * LP + k], acc[k]);
       }
+    }
+    if (sl >= 0) {
+#pragma unroll
+      for (int k = 0; k < LP; ++k) acc[k] = 0.f;
     }
     if (xhat) {
       float4* xo = reinterpret_cast<float4*>(xhat + i * LP);
@@ -1848,37 +1790,41 @@ k_jacobi_grid(const float* __restrict__ xin, float* __restrict__ xout,
   float4 xv[NV];
 #pragma unroll
   for (int t = 0; t < NV; ++t) xv[t] = xi4[i * NV + t];
+  // every load of the step is issued before the seed flag is tested (one round trip); seed
+  // rows keep their value
   const int sl = seedlab[i];
-  if (sl < 0) {
-    float4 acc[NV];
+  float4 acc[NV];
 #pragma unroll
-    for (int t = 0; t < NV; ++t) acc[t] = make_float4(0.f, 0.f, 0.f, 0.f);
-    auto add = [&](int64_t j, float c) {
-#pragma unroll
-      for (int t = 0; t < NV; ++t) {
-        const float4 v = xi4[j * NV + t];
-        acc[t].x = fmaf(c, v.x, acc[t].x); acc[t].y = fmaf(c, v.y, acc[t].y);
-        acc[t].z = fmaf(c, v.z, acc[t].z); acc[t].w = fmaf(c, v.w, acc[t].w);
-      }
-    };
-    if (x > 0) add(i - 1, cw[i - 1]);
-    if (x + 1 < DX) add(i + 1, cw[i]);
-    if (y > 0) add(i - sy, cw[N + i - sy]);
-    if (y + 1 < DY) add(i + sy, cw[N + i]);
-    if (ndim == 3) {
-      if (z > 0) add(i - sz, cw[2 * N + i - sz]);
-      if (z + 1 < DZ) add(i + sz, cw[2 * N + i]);
-    }
-    const float aii = (normalized ? 1.f : d[i]) + gamma;
-    const float f = omega / aii, keep = 1.f - omega;
-    const float4* p4 = reinterpret_cast<const float4*>(phat);
+  for (int t = 0; t < NV; ++t) acc[t] = make_float4(0.f, 0.f, 0.f, 0.f);
+  auto add = [&](int64_t j, float c) {
 #pragma unroll
     for (int t = 0; t < NV; ++t) {
-      const float4 pv = p4[i * NV + t];
-      xv[t].x = keep * xv[t].x + f * fmaf(gamma, pv.x, acc[t].x);
-      xv[t].y = keep * xv[t].y + f * fmaf(gamma, pv.y, acc[t].y);
-      xv[t].z = keep * xv[t].z + f * fmaf(gamma, pv.z, acc[t].z);
-      xv[t].w = keep * xv[t].w + f * fmaf(gamma, pv.w, acc[t].w);
+      const float4 v = xi4[j * NV + t];
+      acc[t].x = fmaf(c, v.x, acc[t].x); acc[t].y = fmaf(c, v.y, acc[t].y);
+      acc[t].z = fmaf(c, v.z, acc[t].z); acc[t].w = fmaf(c, v.w, acc[t].w);
+    }
+  };
+  if (x > 0) add(i - 1, cw[i - 1]);
+  if (x + 1 < DX) add(i + 1, cw[i]);
+  if (y > 0) add(i - sy, cw[N + i - sy]);
+  if (y + 1 < DY) add(i + sy, cw[N + i]);
+  if (ndim == 3) {
+    if (z > 0) add(i - sz, cw[2 * N + i - sz]);
+    if (z + 1 < DZ) add(i + sz, cw[2 * N + i]);
+  }
+  const float aii = (normalized ? 1.f : d[i]) + gamma;
+  const float4* p4 = reinterpret_cast<const float4*>(phat);
+  float4 pv[NV];
+#pragma unroll
+  for (int t = 0; t < NV; ++t) pv[t] = p4[i * NV + t];
+  if (sl < 0) {
+    const float f = omega / aii, keep = 1.f - omega;
+#pragma unroll
+    for (int t = 0; t < NV; ++t) {
+      xv[t].x = keep * xv[t].x + f * fmaf(gamma, pv[t].x, acc[t].x);
+      xv[t].y = keep * xv[t].y + f * fmaf(gamma, pv[t].y, acc[t].y);
+      xv[t].z = keep * xv[t].z + f * fmaf(gamma, pv[t].z, acc[t].z);
+      xv[t].w = keep * xv[t].w + f * fmaf(gamma, pv[t].w, acc[t].w);
     }
   }
   if (!last) {
@@ -1948,7 +1894,7 @@ rw_status launch_proj_back(bool back, const T* Q, int ldq, const float* phat,
       RW_LAUNCH((k_project_cw<T, LP>), nblk, 256, shm, st, Q, g->N, nchunk, phat, seedlab, mdev,
                 rpb, part);
     } else {
-      const size_t shm = sizeof(float) * (size_t)((nchunk + 3) / 4 * 4) * 8 * LP;
+      const size_t shm = sizeof(float) * (size_t)((nchunk + kBackChunks - 1) / kBackChunks * kBackChunks) * 8 * LP;
       RW_LAUNCH((k_backproject_panel<T, LP>), nblk, 256, shm, st, Q, g->N, nchunk, C, cscale, seedlab,
                                                         g->sq, g->s, L, mdev, xhat, U, labels, clear);
     }
@@ -2057,16 +2003,18 @@ rw_status rw_solve_priors_internal(const rw_graph* g, const int32_t* seed_idx,
   if (!ws.seeds_clean)
     RW_LAUNCH(k_seed_reset, rw_blocks(g->N, 256), 256, 0, st, seedlab, g->N, nullptr, 0);
   ws.seeds_clean = false;
+  const int sms = g_rw_num_sms > 0 ? g_rw_num_sms : 148;
+  const int pblk = (int)std::min<int64_t>(rw_blocks(g->N, 256), 8 * sms);
   RW_LAUNCH(k_seed_scatter, nsb, 256, 0, st, seed_idx, seed_lab, S, L, g->N,
             g->J ? g->J : nullptr, seedlab, bpart, g->status);
   if (lp == 4)
-    RW_LAUNCH(k_priors<4>, rw_blocks(g->N, 256), 256, 0, st, g->J, g->sq, g->N, L, prior_mode,
+    RW_LAUNCH(k_priors<4>, pblk, 256, 0, st, g->J, g->sq, g->N, L, prior_mode,
               bpart, nsb, fit64, priors, ws.phat.as<float>(), g->status);
   else if (lp == 8)
-    RW_LAUNCH(k_priors<8>, rw_blocks(g->N, 256), 256, 0, st, g->J, g->sq, g->N, L, prior_mode,
+    RW_LAUNCH(k_priors<8>, pblk, 256, 0, st, g->J, g->sq, g->N, L, prior_mode,
               bpart, nsb, fit64, priors, ws.phat.as<float>(), g->status);
   else
-    RW_LAUNCH(k_priors<16>, rw_blocks(g->N, 256), 256, 0, st, g->J, g->sq, g->N, L, prior_mode,
+    RW_LAUNCH(k_priors<16>, pblk, 256, 0, st, g->J, g->sq, g->N, L, prior_mode,
               bpart, nsb, fit64, priors, ws.phat.as<float>(), g->status);
   *phat_out = ws.phat.as<float>();
   *seedlab_out = seedlab;
