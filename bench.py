@@ -192,10 +192,10 @@ def phase_work(phase, N, m, lp, S, L, steps):
         return "hbm", N * (4 + 4 + 4 * lp), "B"
     if phase == "gather":    # seed rows of Q and neighbour rows (FP32), Gram of [X Q_s r U]
         return "alu", 2.0 * S * m * (2 * m + 2 * lp), "flop"
-    if phase == "adapt":     # Cholesky of G_m + solves for the labels
-        return "alu", m ** 3 / 3.0 + 2.0 * L * m * m, "flop"
-    if phase == "small":     # LU of the m x m Woodbury matrix + solves
-        return "alu", 2.0 * m ** 3 / 3.0 + 2.0 * L * m * m, "flop"
+    if phase == "adapt":     # Cholesky of G_m + solves for the labels, LU of the m x m system
+        return "alu", m ** 3 / 3.0 + 2.0 * L * m * m + 2.0 * m ** 3 / 3.0, "flop"
+    if phase == "small":     # the two triangular solves per label
+        return "alu", 2.0 * L * m * m, "flop"
     if phase == "project":   # 16-bit basis rows (m cols) + hat priors + seed labels
         return "hbm", N * (2 * m + 4 * lp + 4), "B"
     if phase == "back":      # basis rows again + write U-hat (lp) + seed labels + d^{1/2}
@@ -206,8 +206,8 @@ def phase_work(phase, N, m, lp, S, L, steps):
 
 
 PHASE_KERNELS = {"seeds": "k_seed_scatter+k_priors",
-                 "gather": "k_seed_gather+k_seed_gram", "adapt": "k_adapt",
-                 "project": "k_project_cw+k_reduce_partials", "small": "k_small_solve",
+                 "gather": "k_seed_gather+k_seed_gram", "adapt": "k_adapt_lu",
+                 "project": "k_project_cw+k_reduce_partials", "small": "k_small_rhs",
                  "back": "k_backproject_panel", "refine": "k_jacobi_grid x3"}
 
 

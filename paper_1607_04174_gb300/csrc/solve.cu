@@ -36,12 +36,13 @@ constexpr int kMaxSeeds = 65536;   // seeds per solve (the validation's limit)  
 int lpad_of(int L) { return L <= 4 ? 4 : (L <= 8 ? 8 : 16); }
 
 struct Layout {
-  size_t mdev, Bcat, Gcat, Z, C, fu, nrm, cand, Lg, zg, scal, part, total;
+  size_t mdev, Bcat, Gcat, Z, C, fu, lu, luinv, part, total;
 };
 
 // wcat = 2 mp + 2 lp: the seed-side block [X | Q_s | r0 | U-hat_s] (S x wcat, one row per
 // seed) and its product with Q_s, [K | G | h | b] = Q_s^T [X | Q_s | r0 | U-hat_s] (mp x wcat)
 Layout make_layout(int S, int mp, int mq, int lp, int L, int ncand, int nblk_part) {
+  (void)L;
   Layout o;
   size_t off = 0;
   auto take = [&](size_t bytes) { size_t r = off; off += (bytes + 255) & ~size_t(255); return r; };
@@ -52,11 +53,8 @@ Layout make_layout(int S, int mp, int mq, int lp, int L, int ncand, int nblk_par
   o.Z = take(sizeof(float) * (size_t)mq * lp + sizeof(float) * (size_t)mq);  // Z, lambda + gamma
   o.C = take(sizeof(float) * (size_t)mq * lp);
   o.fu = take(sizeof(double) * (size_t)(ncand + 1) * RW_MAX_LABELS + sizeof(double) * lp);
-  o.nrm = take(sizeof(float) * (size_t)(ncand + 1) * RW_MAX_LABELS);
-  o.cand = take(sizeof(int) * (size_t)(ncand + 1));
-  o.Lg = take(sizeof(float) * (size_t)mp * mp);
-  o.zg = take(sizeof(float) * (size_t)L * mp);
-  o.scal = take(sizeof(float) * 8);
+  o.lu = take(sizeof(float) * (size_t)mp * mp);   // LU factors of the m x m system, pitch mp
+  o.luinv = take(sizeof(float) * (size_t)mp);     // 1 / U_ii
   o.part = take(sizeof(float) * (size_t)nblk_part * mq * lp);
   o.total = off;
   return o;
@@ -67,6 +65,16 @@ __device__ __forceinline__ float warp_sum(float v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffff, v, o);
   return v;
 }
+
+__device__ __forceinline__ void cp_async4(float* dst, const float* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;"
+               :: "r"((unsigned)__cvta_generic_to_shared(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async16(float* dst, const float* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;"
+               :: "r"((unsigned)__cvta_generic_to_shared(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 // ---------------------------------------------------------------------------------------
 __global__ void k_seed_reset(int* __restrict__ seedlab, int64_t n, double* __restrict__ stats,
@@ -340,6 +348,103 @@ __device__ void gemm_trailing(float* A, int ms, int m, int ncol, int r1, int p0,
   }
 }
 
+// A[i][j] -= sum_{q < 32} A[i][p0 + q] A[p0 + q][j] for i in [i0, i1), j in [j0, j1): warp
+// tasks of RU rows x 32 NV columns (lane = column within each 32-column group)
+template <int RU, int NV>
+__device__ void gemm_rect(float* A, int ms, int i0, int i1, int j0, int j1, int p0) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int n = i1 - i0, nc = j1 - j0;
+  if (n <= 0 || nc <= 0) return;
+  const int nrt = (n + RU - 1) / RU, nct = (nc + 32 * NV - 1) / (32 * NV);
+  for (int task = warp; task < nrt * nct; task += nw) {
+    const int ib = i0 + RU * (task / nct), jb = j0 + 32 * NV * (task % nct) + lane;
+    float acc[RU][NV];
+#pragma unroll
+    for (int u = 0; u < RU; ++u)
+#pragma unroll
+      for (int v = 0; v < NV; ++v) acc[u][v] = 0.f;
+#pragma unroll 2
+    for (int q = 0; q < 32; ++q) {
+      float av[RU], bv[NV];
+#pragma unroll
+      for (int u = 0; u < RU; ++u) av[u] = A[min(ib + u, i1 - 1) * ms + p0 + q];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) bv[v] = A[(p0 + q) * ms + min(jb + 32 * v, j1 - 1)];
+#pragma unroll
+      for (int u = 0; u < RU; ++u)
+#pragma unroll
+        for (int v = 0; v < NV; ++v) acc[u][v] = fmaf(av[u], bv[v], acc[u][v]);
+    }
+#pragma unroll
+    for (int u = 0; u < RU; ++u)
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        const int i = ib + u, j = jb + 32 * v;
+        if (i < i1 && j < j1) A[i * ms + j] -= acc[u][v];
+      }
+  }
+}
+
+// The same update for a row stride that is a multiple of 4 and p0, j0 multiples of 4: both
+// operands move as 16-byte loads.  A warp task covers RU (32 / LC) rows x 4 LC columns: lane
+// (lr = lane / LC, lc = lane % LC) owns rows ib + lr RU + u and the four columns jb + 4 lc ..;
+// per four steps of q, RU loads of the row operand and four of the column operand feed 16 RU
+// FMAs.
+template <int RU, int LC>
+__device__ void gemm4(float* A, int ms, int i0, int i1, int j0, int j1, int p0) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  constexpr int TR = RU * (32 / LC), TC = 4 * LC;
+  const int n = i1 - i0, nc = j1 - j0;
+  if (n <= 0 || nc <= 0) return;
+  const int nrt = (n + TR - 1) / TR, nct = (nc + TC - 1) / TC;
+  const int lr = lane / LC, lc = lane % LC;
+  for (int task = warp; task < nrt * nct; task += nw) {
+    const int ib = i0 + TR * (task / nct) + RU * lr, jb = j0 + TC * (task % nct) + 4 * lc;
+    const int jl = min(jb, j1 - 1) & ~3;  // loads stay inside the row (ms >= round_up(j1, 4))
+    float acc[RU][4];
+#pragma unroll
+    for (int u = 0; u < RU; ++u)
+#pragma unroll
+      for (int v = 0; v < 4; ++v) acc[u][v] = 0.f;
+    const float* brow = A + (size_t)p0 * ms + jl;
+    for (int q4 = 0; q4 < 8; ++q4) {
+      float4 av[RU], bv[4];
+#pragma unroll
+      for (int u = 0; u < RU; ++u)
+        av[u] = *reinterpret_cast<const float4*>(A + (size_t)min(ib + u, i1 - 1) * ms + p0 + 4 * q4);
+#pragma unroll
+      for (int qq = 0; qq < 4; ++qq)
+        bv[qq] = *reinterpret_cast<const float4*>(brow + (size_t)(4 * q4 + qq) * ms);
+#pragma unroll
+      for (int u = 0; u < RU; ++u) {
+        const float a4[4] = {av[u].x, av[u].y, av[u].z, av[u].w};
+#pragma unroll
+        for (int qq = 0; qq < 4; ++qq) {
+          acc[u][0] = fmaf(a4[qq], bv[qq].x, acc[u][0]);
+          acc[u][1] = fmaf(a4[qq], bv[qq].y, acc[u][1]);
+          acc[u][2] = fmaf(a4[qq], bv[qq].z, acc[u][2]);
+          acc[u][3] = fmaf(a4[qq], bv[qq].w, acc[u][3]);
+        }
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < RU; ++u)
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        const int i = ib + u, j = jb + v;
+        if (i < i1 && j < j1) A[(size_t)i * ms + j] -= acc[u][v];
+      }
+  }
+}
+
+// row stride of the LU CTA's matrix: a multiple of 4 (16-byte rows) that is an odd multiple of
+// 4, so that column walks meet at most 4-way bank conflicts
+__host__ __device__ inline int lu_stride(int m) {
+  int s = (m + 3) / 4 * 4;
+  if ((s / 4) % 2 == 0) s += 4;
+  return s;
+}
+
 // one warp: U x = y for the upper factor held in A (uinv = 1 / diag(U)), one register group of
 // 32 rows at a time.  Lane t keeps entries t + 32 q (m <= 224) in registers; each newly final
 // entry is broadcast by shuffle.  The register group of the pivot is a compile-time index, so a
@@ -368,14 +473,19 @@ __device__ __forceinline__ void lu_bwd_group(const float* A, int m, int ms, cons
 // kernels run once per launch on one SM, where code size costs more than loop overhead) and
 // every register index is a constant.
 // ---------------------------------------------------------------------------------------
-__device__ __forceinline__ void shift_update(float (&a)[32], float f, const float* b) {
+__device__ __forceinline__ void load_bcast(float4 (&v)[8], const float* b) {
+#pragma unroll
+  for (int t4 = 0; t4 < 8; ++t4) v[t4] = reinterpret_cast<const float4*>(b)[t4];
+}
+// a[t] <- a[t + 1] - f v[t] with the broadcast vector already in registers (its loads are
+// issued before the scalar chain that produces f)
+__device__ __forceinline__ void shift_update_r(float (&a)[32], float f, const float4 (&v)[8]) {
 #pragma unroll
   for (int t4 = 0; t4 < 8; ++t4) {
-    const float4 v = reinterpret_cast<const float4*>(b)[t4];
-    a[4 * t4 + 0] = fmaf(-f, v.x, a[4 * t4 + 1]);
-    a[4 * t4 + 1] = fmaf(-f, v.y, a[4 * t4 + 2]);
-    a[4 * t4 + 2] = fmaf(-f, v.z, a[4 * t4 + 3]);
-    a[4 * t4 + 3] = (t4 < 7) ? fmaf(-f, v.w, a[4 * t4 + 4]) : 0.f;
+    a[4 * t4 + 0] = fmaf(-f, v[t4].x, a[4 * t4 + 1]);
+    a[4 * t4 + 1] = fmaf(-f, v[t4].y, a[4 * t4 + 2]);
+    a[4 * t4 + 2] = fmaf(-f, v[t4].z, a[4 * t4 + 3]);
+    a[4 * t4 + 3] = (t4 < 7) ? fmaf(-f, v[t4].w, a[4 * t4 + 4]) : 0.f;
   }
 }
 
@@ -401,6 +511,8 @@ __device__ void chol_diag_rot(float* A, int ms, int k0, int kb, float* dinv, flo
     else if (lane == kk) b[32] = a[0];       // pivot
     __syncwarp();
     float d = b[32];
+    float4 v[8];
+    load_bcast(v, b);
     if (!(d > 0.f)) {
       if (lane == kk) *bad = 1;
       d = 1e-30f;
@@ -412,7 +524,7 @@ __device__ void chol_diag_rot(float* A, int ms, int k0, int kb, float* dinv, flo
       row[kk] = d * ri;                          // L_kk = sqrt(d)
       dinv[kk] = ri;
     }
-    shift_update(a, f, b);
+    shift_update_r(a, f, v);
   }
   __syncwarp();
 }
@@ -422,10 +534,9 @@ __device__ void chol_diag_rot(float* A, int ms, int k0, int kb, float* dinv, flo
 // broadcast from lane kk by shuffles (one per register of the shifted row).  Also writes the
 // shifted copies used by the panel solves: Ush[c][t] = U_c,c+1+t and Lsh[c][t] = L_c+1+t,c
 // (32 x 32 each, zero outside the block).  A pivot below 1e-3 dref (the original row scale) sets
-// *unstable.
+// *unstable (no check when dref is null; a zero pivot is replaced by 1e-30 either way).
 __device__ void lu_diag_rot(float* A, int ms, int k0, int kb, float* buf, const float* dref,
                             float* uinv, float* Ush, float* Lsh, int* unstable) {
-  (void)buf;
   const int lane = threadIdx.x & 31;
   const bool live = lane < kb;
   float* row = A + (size_t)(k0 + (live ? lane : 0)) * ms + k0;
@@ -437,28 +548,37 @@ __device__ void lu_diag_rot(float* A, int ms, int k0, int kb, float* buf, const 
     a[c] = v;
   }
 #pragma unroll
-  for (int t = 0; t < 32; ++t) { Ush[lane * 32 + t] = 0.f; Lsh[lane * 32 + t] = 0.f; }
-  __syncwarp();
+  for (int t = 0; t < 32; ++t) Lsh[lane * 32 + t] = 0.f;
   for (int kk = 0; kk < kb; ++kk) {
-    float u = __shfl_sync(0xffffffff, a[0], kk);
-    if (!(fabsf(u) >= 1e-3f * dref[k0 + kk])) {
-      if (lane == 0) *unstable = 1;
-      if (u == 0.f) u = 1e-30f;
-    }
-    const bool below = lane > kk;
-    const float f = __fdividef(a[0], u);
-    if (below && live) {
-      row[kk] = f;
-      Lsh[kk * 32 + lane - kk - 1] = f;
-    }
+    // the pivot lane publishes its row shifted by one (U_kk,kk+1+t at b[t]) and the pivot
+    float* b = buf + 64 * (kk & 1);
+    if (lane == kk) {
 #pragma unroll
-    for (int t = 0; t < 32; ++t) {
-      const float nxt = t < 31 ? a[t + 1] : 0.f;
-      const float v = __shfl_sync(0xffffffff, nxt, kk);
-      if (below) a[t] = fmaf(-f, v, nxt);
+      for (int t4 = 0; t4 < 8; ++t4)
+        reinterpret_cast<float4*>(b)[t4] =
+            make_float4(a[4 * t4 + 1], a[4 * t4 + 2], a[4 * t4 + 3], t4 < 7 ? a[4 * t4 + 4] : 0.f);
+      b[32] = a[0];
+    }
+    __syncwarp();
+    float u = b[32];
+    float4 v[8];
+    load_bcast(v, b);
+    if (dref && !(fabsf(u) >= 1e-3f * dref[k0 + kk]) && lane == 0) *unstable = 1;
+    if (u == 0.f) u = 1e-30f;
+    if (lane > kk) {
+      const float f = __fdividef(a[0], u);
+      if (live) {
+        row[kk] = f;
+        Lsh[kk * 32 + lane - kk - 1] = f;
+      }
+      shift_update_r(a, f, v);  // rows above and at the pivot keep their U rows
     }
   }
+  __syncwarp();
   // lane r stopped shifting at step r: a[t] = U_r,r+t
+#pragma unroll
+  for (int t = 0; t < 32; ++t) Ush[lane * 32 + t] = 0.f;
+  __syncwarp();
   if (live) {
 #pragma unroll
     for (int t = 0; t < 32; ++t) {
@@ -472,6 +592,130 @@ __device__ void lu_diag_rot(float* A, int ms, int k0, int kb, float* buf, const 
   __syncwarp();
 }
 
+// ---------------------------------------------------------------------------------------
+// 32 x 32 blocks on 128 threads: thread t keeps eight entries of row (or column) t / 4, the
+// quarter t % 4, in registers, so a step is eight FMAs per thread.  Values of another quarter of
+// the same row come by a shuffle inside the row's four lanes; what every row needs (a pivot row
+// or column) goes through shared memory with one named barrier per step (double-buffered).
+// The step loop runs over the owning quarter (rolled) and the entry inside it (unrolled), so
+// every register index is a constant.
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ void bar_sync_128() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+
+__device__ __forceinline__ void unpack8(const float4& v0, const float4& v1, float (&p)[8]) {
+  p[0] = v0.x; p[1] = v0.y; p[2] = v0.z; p[3] = v0.w;
+  p[4] = v1.x; p[5] = v1.y; p[6] = v1.z; p[7] = v1.w;
+}
+
+// LU without pivoting of the kb x kb diagonal block at (k0, k0) by threads 0..127 (unit-lower
+// multipliers below the diagonal, U on and above); uinv[k0 + c] = 1 / U_cc.  P: 80 floats,
+// 16-byte aligned.  A pivot below 1e-3 dref (when dref is given) sets *unstable; a zero pivot is
+// replaced by 1e-30.
+__device__ void lu_diag_128(float* A, int ms, int k0, int kb, float* P, float* uinv,
+                            const float* dref, int* unstable) {
+  const int t = threadIdx.x, r = t >> 2, g = t & 3, src = (t & 31) & ~3;
+  const bool live = r < kb;
+  float* row = A + (size_t)(k0 + (live ? r : 0)) * ms + k0 + 8 * g;
+  float a[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) a[q] = (live && 8 * g + q < kb) ? row[q] : 0.f;
+  for (int go = 0; go < 4; ++go) {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int kk = 8 * go + j;
+      if (kk < kb) {
+        float* p = P + 40 * (kk & 1);
+        if (r == kk) {
+          reinterpret_cast<float4*>(p)[2 * g] = make_float4(a[0], a[1], a[2], a[3]);
+          reinterpret_cast<float4*>(p)[2 * g + 1] = make_float4(a[4], a[5], a[6], a[7]);
+        }
+        const float ark = __shfl_sync(0xffffffff, a[j], src | go);  // A_r,kk from its owner
+        bar_sync_128();
+        float pv[8];
+        unpack8(reinterpret_cast<const float4*>(p)[2 * g], reinterpret_cast<const float4*>(p)[2 * g + 1], pv);
+        float u = p[kk];
+        if (dref && t == 0 && !(fabsf(u) >= 1e-3f * dref[k0 + kk])) *unstable = 1;
+        if (u == 0.f) u = 1e-30f;
+        if (t == 4 * kk) uinv[k0 + kk] = 1.f / u;
+        if (r > kk) {
+          const float f = __fdividef(ark, u);
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            const int col = 8 * g + q;
+            if (col > kk) a[q] = fmaf(-f, pv[q], a[q]);
+            else if (col == kk) a[q] = f;
+          }
+        }
+      }
+    }
+  }
+  if (live) {
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+      if (8 * g + q < kb) row[q] = a[q];
+  }
+  bar_sync_128();
+}
+
+// Rows r0 .. r0 + nr of the 32 columns at c0 times U^{-1} (U the block at (c0, c0)): threads
+// tb .. tb + 127, four per row.  U32[c][col] = U_c,col for col > c, else 0; ui = 1 / diag(U).
+__device__ void trsm_rows_128(float* A, int ms, int r0, int nr, int c0, const float* U32,
+                              const float* ui, int tb) {
+  const int t = threadIdx.x - tb, r = t >> 2, g = t & 3, src = (t & 31) & ~3;
+  const bool live = r < nr;
+  float* row = A + (size_t)(r0 + (live ? r : 0)) * ms + c0 + 8 * g;
+  float a[8], uv[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    a[q] = live ? row[q] : 0.f;
+    uv[q] = ui[c0 + 8 * g + q];
+  }
+  for (int go = 0; go < 4; ++go) {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int c = 8 * go + j;
+      float w[8];
+      unpack8(reinterpret_cast<const float4*>(U32 + c * 32)[2 * g],
+              reinterpret_cast<const float4*>(U32 + c * 32)[2 * g + 1], w);
+      const float x = __shfl_sync(0xffffffff, a[j] * uv[j], src | go);
+      if (g == go) a[j] = x;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) a[q] = fmaf(-x, w[q], a[q]);  // zero where col <= c
+    }
+  }
+  if (live) {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) row[q] = a[q];
+  }
+}
+
+// Columns r0 .. r0 + nc of the 32 rows at c0 premultiplied by L^{-1} (L unit lower, the block at
+// (c0, c0)): threads tb .. tb + 127, four per column.  L32T[r][row] = L_row,r for row > r, else 0.
+__device__ void trsm_cols_128(float* A, int ms, int r0, int nc, int c0, const float* L32T, int tb) {
+  const int t = threadIdx.x - tb, cc = t >> 2, g = t & 3, src = (t & 31) & ~3;
+  const bool live = cc < nc;
+  float* col = A + (size_t)(c0 + 8 * g) * ms + r0 + (live ? cc : 0);
+  float a[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) a[q] = live ? col[(size_t)q * ms] : 0.f;
+  for (int go = 0; go < 4; ++go) {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int rr = 8 * go + j;
+      float l[8];
+      unpack8(reinterpret_cast<const float4*>(L32T + rr * 32)[2 * g],
+              reinterpret_cast<const float4*>(L32T + rr * 32)[2 * g + 1], l);
+      const float y = __shfl_sync(0xffffffff, a[j], src | go);
+#pragma unroll
+      for (int q = 0; q < 8; ++q) a[q] = fmaf(-y, l[q], a[q]);  // zero where row <= rr
+    }
+  }
+  if (live) {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) col[(size_t)q * ms] = a[q];
+  }
+}
+
 // x = a U^{-1} for one row a (kb entries at ar), U the block whose shifted rows are in Ush and
 // whose reciprocal diagonal is ui (right-looking, shifted registers)
 __device__ __forceinline__ void trsm_row_rot(float* ar, int kb, const float* Ush, const float* ui) {
@@ -479,9 +723,11 @@ __device__ __forceinline__ void trsm_row_rot(float* ar, int kb, const float* Ush
 #pragma unroll
   for (int c = 0; c < 32; ++c) a[c] = c < kb ? ar[c] : 0.f;
   for (int c = 0; c < kb; ++c) {
+    float4 v[8];
+    load_bcast(v, Ush + c * 32);
     const float x = a[0] * ui[c];
     ar[c] = x;
-    shift_update(a, x, Ush + c * 32);
+    shift_update_r(a, x, v);
   }
 }
 
@@ -492,9 +738,11 @@ __device__ __forceinline__ void trsm_col_rot(float* ac, int ms, int kb, const fl
 #pragma unroll
   for (int r = 0; r < 32; ++r) a[r] = r < kb ? ac[r * ms] : 0.f;
   for (int r = 0; r < kb; ++r) {
+    float4 v[8];
+    load_bcast(v, Lsh + r * 32);
     const float y = a[0];
     ac[r * ms] = y;
-    shift_update(a, y, Lsh + r * 32);
+    shift_update_r(a, y, v);
   }
 }
 
@@ -786,14 +1034,15 @@ k_seed_gram(const float* __restrict__ A, int lda, const float* __restrict__ B, i
 // trust-region solution (Newton on 1/||a(mu)|| - 1/rho, a Cholesky of G_m + mu I per step) is
 // computed for it and, if it fails, for the following candidates.
 // ---------------------------------------------------------------------------------------
+// hint_remote / final_remote (null when the CTA runs alone): mailboxes in the shared memory of
+// the LU CTA of the cluster, told the first passing candidate as soon as it is found and the
+// final m at the end
 template <int LP>
-__global__ void __launch_bounds__(256, 1)
-k_adapt(const float* __restrict__ G, int ldg, const float* __restrict__ bv, int ldb,
-        const float* __restrict__ Qs, int ldq, const float* __restrict__ Us, int ldu, int S,
-        int L, int mmax, int mstep, double rho, double fmax, int* __restrict__ mdev,
-        double* __restrict__ fsel) {
-  rw_grid_wait();
-  rw_grid_trigger();
+__device__ void adapt_body(const float* __restrict__ G, int ldg, const float* __restrict__ bv,
+                           int ldb, const float* __restrict__ Qs, int ldq,
+                           const float* __restrict__ Us, int ldu, int S, int L, int mmax,
+                           int mstep, double rho, double fmax, int* __restrict__ mdev,
+                           double* __restrict__ fsel, int* hint_remote, int* final_remote) {
   extern __shared__ float sm[];
   const int ms = mmax | 1;
   float* A = sm;                          // mmax x ms, lower factor
@@ -846,10 +1095,13 @@ k_adapt(const float* __restrict__ G, int ldg, const float* __restrict__ bv, int 
   int rows_done = 0;
   for (int K = 0; K * 32 < mmax; ++K) {
     const int r0 = K * 32, nr = min(32, mmax - r0);
-    // tile row K of G + mu0 I (columns 0 .. r0 + nr)
+    // tile row K of G + mu0 I (columns 0 .. r0 + nr): every element requested at once
+    // (cp.async), then the shift on the diagonal
     for (int i = r0 + warp; i < r0 + nr; i += nw)
-      for (int j = lane; j <= i; j += 32)
-        A[i * ms + j] = G[(int64_t)i * ldg + j] + (i == j ? mu0 : 0.f);
+      for (int j = lane; j <= i; j += 32) cp_async4(A + i * ms + j, G + (int64_t)i * ldg + j);
+    cp_async_wait_all();
+    __syncthreads();
+    if (tid < nr) A[(r0 + tid) * ms + r0 + tid] += mu0;
     __syncthreads();
     // off-diagonal tiles L_KJ = (A_KJ - sum_{t<J} L_Kt L_Jt^T) L_JJ^{-T}, J = 0..K-1 in order
     for (int J = 0; J < K; ++J) {
@@ -942,7 +1194,10 @@ k_adapt(const float* __restrict__ G, int ldg, const float* __restrict__ bv, int 
       }
     }
     __syncthreads();
-    if (chosen >= 0) break;
+    if (chosen >= 0) {
+      if (tid == 0 && hint_remote) *reinterpret_cast<volatile int*>(hint_remote) = cand_m(chosen);
+      break;
+    }
   }
   if (tid == 0 && chosen < 0) { chosen = ncand - 1; capped = 1; }
   __syncthreads();
@@ -1038,7 +1293,23 @@ k_adapt(const float* __restrict__ G, int ldg, const float* __restrict__ bv, int 
     mdev[0] = cand_m(c);
     mdev[1] = capped;
     for (int k = 0; k < L; ++k) fsel[k] = fk[k];
+    if (final_remote) {
+      *reinterpret_cast<volatile int*>(hint_remote) = cand_m(c);
+      *reinterpret_cast<volatile int*>(final_remote) = cand_m(c);
+    }
   }
+}
+
+template <int LP>
+__global__ void __launch_bounds__(256, 1)
+k_adapt(const float* __restrict__ G, int ldg, const float* __restrict__ bv, int ldb,
+        const float* __restrict__ Qs, int ldq, const float* __restrict__ Us, int ldu, int S,
+        int L, int mmax, int mstep, double rho, double fmax, int* __restrict__ mdev,
+        double* __restrict__ fsel) {
+  rw_grid_wait();
+  rw_grid_trigger();
+  adapt_body<LP>(G, ldg, bv, ldb, Qs, ldq, Us, ldu, S, L, mmax, mstep, rho, fmax, mdev, fsel,
+                 nullptr, nullptr);
 }
 
 __global__ void k_set_m(int* mdev, int m) {
@@ -1169,8 +1440,8 @@ __global__ void k_reduce_partials(const float* __restrict__ part, int nblk, int 
                                   int mq, float scale, float* __restrict__ Z,
                                   const double* __restrict__ lam, double gamma, int m,
                                   float* __restrict__ lgam) {
+  rw_grid_trigger();  // the small solve's prologue only reads results older than the projection
   rw_grid_wait();
-  rw_grid_trigger();
   // one warp per entry of Z: lane l adds the partials l, l + 32, ... in order, then a fixed
   // butterfly; also lgam = lambda + gamma in FP32 for the small system
   const int lane = threadIdx.x & 31;
@@ -1217,13 +1488,11 @@ __device__ void load_M(float* M, int m, int ms, const float* __restrict__ K, int
 }
 
 template <int LP>
-__global__ void __launch_bounds__(256, 1)
-k_small_solve(const float* __restrict__ K, int ldk, const float* __restrict__ h, int ldh,
-              const float* __restrict__ Z, const float* __restrict__ lgam, float gamma,
-              int L, int lp, int mq, const int* __restrict__ mdev, float* __restrict__ C,
-              int* status) {
-  rw_grid_wait();
-  rw_grid_trigger();
+__device__ void small_solve_body(const float* __restrict__ K, int ldk, const float* __restrict__ h,
+                                 int ldh, const float* __restrict__ Z,
+                                 const float* __restrict__ lgam, float gamma, int L, int lp,
+                                 int mq, const int* __restrict__ mdev, float* __restrict__ C,
+                                 int* status) {
   extern __shared__ float sm[];
   const int m = mdev[0];
   const int na = m + L;                // augmented columns: [M | B]
@@ -1391,6 +1660,360 @@ k_small_solve(const float* __restrict__ K, int ldk, const float* __restrict__ h,
     }
   }
   if (threadIdx.x == 0 && bad) atomicOr(status, RW_DEV_SINGULAR);
+}
+
+template <int LP>
+__global__ void __launch_bounds__(256, 1)
+k_small_solve(const float* __restrict__ K, int ldk, const float* __restrict__ h, int ldh,
+              const float* __restrict__ Z, const float* __restrict__ lgam, float gamma,
+              int L, int lp, int mq, const int* __restrict__ mdev, float* __restrict__ C,
+              int* status) {
+  rw_grid_wait();
+  rw_grid_trigger();
+  small_solve_body<LP>(K, ldk, h, ldh, Z, lgam, gamma, L, lp, mq, mdev, C, status);
+}
+
+// ---------------------------------------------------------------------------------------
+// The adaptive choice of m and the factorization of the m x m system as one cluster of two
+// CTAs.  M = diag(lambda + gamma) - K does not depend on the projection, and an LU without
+// pivoting of M restricted to its leading rows and columns is the leading part of the LU of M,
+// so the LU CTA factors M tile by tile (left-looking) while the other CTA grows its Cholesky
+// over the candidates; it stops at the first tile boundary past the m it is told.  After the
+// projection, C = M^{-1} (h + gamma Z) needs only the two triangular solves (with
+// K = diag(lambda + gamma) - M and W = Lambda_gamma Z, h + gamma K W = h + gamma Z - gamma M W,
+// so y + gamma W = M^{-1} (h + gamma Z)).
+// ---------------------------------------------------------------------------------------
+constexpr int kLuTiles = kMaxSmallM / 32;  // column tiles per row of the stability maxima
+
+__device__ __forceinline__ void bar_sync_id(int id, int nthreads) {
+  asm volatile("bar.sync %0, %1;" :: "r"(id), "r"(nthreads) : "memory");
+}
+
+// Tile T of the left-looking LU held in A (stride ms, a multiple of 4; K's pitch ldk too).
+// lu_load_border: the border of M (rows [r0, r1) x columns [0, r1) and rows [0, r0) x columns
+// [r0, r1)) by warps w0.. of the CTA: every 16-byte piece of K is requested at once
+// (cp.async, one round trip), then, after a barrier of those warps (id 2), a thread per (row,
+// column tile) forms M = diag(lambda + gamma) - K in place and dmax[i][q] = max_j |M_ij| over
+// column tile q (the stability check's row scale).  Whole 16-byte pieces past r1 may be copied
+// (inside the row; never read).
+__device__ void lu_load_border(float* A, int ms, int T, int mmax, const float* __restrict__ Kg,
+                               int ldk, const float* lg, float* dmax, int w0) {
+  const int lane = threadIdx.x & 31, warp = (threadIdx.x >> 5) - w0, nw = (blockDim.x >> 5) - w0;
+  const int t = threadIdx.x - 32 * w0, nt = 32 * nw;
+  const int r0 = 32 * T, nr = min(32, mmax - r0), r1 = r0 + nr;
+  const int w4 = (r1 + 3) / 4, c4 = (nr + 3) / 4;
+  for (int i = r0 + warp; i < r1; i += nw)  // row block: a warp per row
+    for (int c = lane; c < w4; c += 32)
+      cp_async16(A + (size_t)i * ms + 4 * c, Kg + (int64_t)i * ldk + 4 * c);
+  for (int ib = 4 * warp; ib < r0; ib += 4 * nw) {  // column block: four rows per warp step
+    const int i = ib + (lane >> 3), c = lane & 7;
+    if (i < r0 && c < c4) cp_async16(A + (size_t)i * ms + r0 + 4 * c, Kg + (int64_t)i * ldk + r0 + 4 * c);
+  }
+  cp_async_wait_all();
+  bar_sync_id(2, nt);
+  const int nrb = nr * (T + 1);
+  for (int e = t; e < nrb + r0; e += nt) {
+    int i, q;
+    if (e < nrb) { i = r0 + e / (T + 1); q = e % (T + 1); }
+    else { i = e - nrb; q = T; }
+    float* ar = A + (size_t)i * ms + 32 * q;
+    const int cnt = min(32, r1 - 32 * q), rot = cnt == 32 ? (e & 31) : 0;  // rotation: spread banks
+    const int dg = i - 32 * q;  // diagonal position inside the tile (if any)
+    float mx = 0.f;
+    for (int k = 0; k < cnt; ++k) {
+      int kk = k + rot;
+      if (kk >= cnt) kk -= cnt;
+      const float v = (kk == dg ? lg[i] : 0.f) - ar[kk];
+      ar[kk] = v;
+      mx = fmaxf(mx, fabsf(v));
+    }
+    dmax[i * kLuTiles + q] = mx;
+  }
+}
+
+// lu_solve_border: the loaded border against the factored blocks J < T in order (the row block
+// against U_JJ, the column block against L_JJ, each solve followed by the update of the rest of
+// the border), all warps; ends with a barrier.  The diagonal block is then factored by one warp
+// (lu_diag_rot) while the other warps load the next tile's border, which no step of this tile
+// reads or writes.
+__device__ void lu_solve_border(float* A, int ms, int T, int mmax, float* Ush, float* Lsh,
+                                const float* uinv) {
+  const int tid = threadIdx.x;
+  const int r0 = 32 * T, nr = min(32, mmax - r0), r1 = r0 + nr;
+  for (int J = 0; J < T; ++J) {
+    const int c0 = 32 * J;
+    // U32[c][col] = U_c,col (col > c) and L32T[r][row] = L_row,r (row > r) of block J, else 0
+    for (int e = tid; e < 1024; e += blockDim.x) {
+      const int c = e >> 5, o = e & 31;
+      Ush[e] = o > c ? A[(c0 + c) * ms + c0 + o] : 0.f;
+      Lsh[e] = o > c ? A[(c0 + o) * ms + c0 + c] : 0.f;
+    }
+    __syncthreads();
+    if (tid < 128) trsm_rows_128(A, ms, r0, nr, c0, Ush, uinv, 0);
+    else trsm_cols_128(A, ms, r0, nr, c0, Lsh, 128);
+    __syncthreads();
+    gemm4<8, 32>(A, ms, r0, r1, c0 + 32, r1, c0);   // row block, columns past block J
+    gemm4<4, 8>(A, ms, c0 + 32, r0, r0, r1, c0);    // column block, rows past block J
+    __syncthreads();
+  }
+}
+
+// The LU CTA: tiles until the adaptive CTA's hint (the first passing candidate) is covered,
+// then the cluster barrier (after which the final m is in the mailbox), then any tiles still
+// missing.  Writes the leading m x m factors (F, pitch ldf), 1 / U_ii and mdev[2] = 1 when a
+// pivot falls below 1e-3 of the largest |M_ij| of its row over the first ceil(m / 32) column
+// tiles (the solve then pivots from the original matrix).
+__device__ void lu_body(cg::cluster_group& cl, int mmax, const float* __restrict__ Kg, int ldk,
+                        const double* __restrict__ lam, double gamma, float* __restrict__ F,
+                        int ldf, float* __restrict__ luinv, int* __restrict__ mdev,
+                        const int* hint, const int* fin) {
+  extern __shared__ float sm[];
+  const int tid = threadIdx.x;
+  const int ms = lu_stride(mmax);
+  float* A = sm;
+  float* dmax = A + (size_t)mmax * ms;
+  __shared__ float lg[kMaxSmallM], uinv[kMaxSmallM];
+  __shared__ __align__(16) float Ush[32 * 32], Lsh[32 * 32];
+  __shared__ __align__(16) float buf[128];
+  __shared__ int dec, unstable, flag;
+  for (int i = tid; i < mmax; i += blockDim.x) lg[i] = (float)(lam[i] + gamma);
+  if (tid == 0) { unstable = 0; flag = 0; }
+  __syncthreads();
+  lu_load_border(A, ms, 0, mmax, Kg, ldk, lg, dmax, 0);
+  __syncthreads();
+  int T = 0, covered = 0, target = mmax;
+  bool synced = false;
+  for (;;) {
+    if (!synced) {
+      if (tid == 0) {
+        int hv;  // the mailbox is this CTA's own shared memory, written remotely by the other CTA
+        asm volatile("ld.volatile.shared.u32 %0, [%1];"
+                     : "=r"(hv) : "r"((unsigned)__cvta_generic_to_shared(hint)));
+        dec = (covered >= mmax || (hv > 0 && covered >= hv)) ? 1 : 0;
+      }
+      __syncthreads();
+      if (dec) {
+        cl.sync();
+        synced = true;
+        target = *reinterpret_cast<const volatile int*>(fin);
+      }
+    }
+    if (synced && covered >= target) break;
+    lu_solve_border(A, ms, T, mmax, Ush, Lsh, uinv);
+    if (threadIdx.x < 128)
+      lu_diag_128(A, ms, 32 * T, min(32, mmax - 32 * T), buf, uinv, nullptr, &flag);
+    else if (32 * (T + 1) < mmax)
+      lu_load_border(A, ms, T + 1, mmax, Kg, ldk, lg, dmax, 4);
+    __syncthreads();
+    ++T;
+    covered = min(32 * T, mmax);
+  }
+  const int m = target, nt = (m + 31) / 32;
+  for (int i = tid; i < m; i += blockDim.x) {
+    float d = 0.f;
+    for (int q = 0; q < nt; ++q) d = fmaxf(d, dmax[i * kLuTiles + q]);
+    const float u = A[i * ms + i];
+    if (u == 0.f || !(fabsf(u) >= 1e-3f * d)) unstable = 1;
+    luinv[i] = uinv[i];
+  }
+  for (int e = tid; e < m * m; e += blockDim.x) {
+    const int i = e / m, j = e - i * m;
+    F[(int64_t)i * ldf + j] = A[i * ms + j];
+  }
+  __syncthreads();
+  if (tid == 0) mdev[2] = unstable;
+}
+
+template <int LP>
+__global__ void __launch_bounds__(256, 1)
+k_adapt_lu(const float* __restrict__ G, int ldg, const float* __restrict__ bv, int ldb,
+           const float* __restrict__ Qs, int ldq, const float* __restrict__ Us, int ldu, int S,
+           int L, int mmax, int mstep, double rho, double fmax, int adaptive,
+           const float* __restrict__ Kg, int ldk, const double* __restrict__ lam, double gamma,
+           float* __restrict__ F, int ldf, float* __restrict__ luinv, int* __restrict__ mdev,
+           double* __restrict__ fsel) {
+  rw_grid_wait();
+  rw_grid_trigger();
+  cg::cluster_group cl = cg::this_cluster();
+  __shared__ int s_hint, s_final;  // mailboxes of the LU CTA
+  if (threadIdx.x == 0) { s_hint = 0; s_final = 0; }
+  cl.sync();  // both CTAs running, mailboxes cleared
+  if (cl.block_rank() == 0) {
+    int* rh = cl.map_shared_rank(&s_hint, 1);
+    int* rf = cl.map_shared_rank(&s_final, 1);
+    if (adaptive) {
+      adapt_body<LP>(G, ldg, bv, ldb, Qs, ldq, Us, ldu, S, L, mmax, mstep, rho, fmax, mdev, fsel,
+                     rh, rf);
+    } else if (threadIdx.x == 0) {
+      mdev[0] = mmax;
+      mdev[1] = 0;
+      *reinterpret_cast<volatile int*>(rh) = mmax;
+      *reinterpret_cast<volatile int*>(rf) = mmax;
+    }
+    cl.sync();
+  } else {
+    lu_body(cl, mmax, Kg, ldk, lam, gamma, F, ldf, luinv, mdev, &s_hint, &s_final);
+  }
+}
+
+// In place, the inverse of the unit-lower diagonal block of A at (r0, r0) (kb x kb), one warp:
+// lane c solves L x = e_c with the column shifted through registers and writes the strictly lower
+// entries of (L^{-1}) over L (entries of L are read one step before their row is written).
+// Touches only the strictly lower triangle of the block.
+__device__ void inv_unit_lower_block(float* A, int ms, int r0, int kb) {
+  const int lane = threadIdx.x & 31;
+  float a[32];
+#pragma unroll
+  for (int t = 0; t < 32; ++t) a[t] = (t == lane) ? 1.f : 0.f;
+  float* blk = A + (size_t)r0 * ms + r0;
+  for (int r = 0; r < kb; ++r) {
+    const float y = a[0];
+    float l[32];
+#pragma unroll
+    for (int t = 0; t < 32; ++t) {
+      const int rr = r + 1 + t;
+      l[t] = rr < kb ? blk[(size_t)rr * ms + r] : 0.f;  // L_{r + 1 + t, r}
+    }
+    __syncwarp();  // lanes stay in step: entry (r, c) is written after every read of it
+    if (lane < r) blk[(size_t)r * ms + lane] = y;
+#pragma unroll
+    for (int t = 0; t < 32; ++t) a[t] = fmaf(-y, l[t], t < 31 ? a[t + 1] : 0.f);
+  }
+}
+
+// In place, the inverse of the upper diagonal block (reciprocal diagonal in ui): lane r solves
+// x U = e_r with the row shifted through registers and writes (U^{-1})_rc for c >= r over U
+// (row c of U is read before any entry of column c is written).  Touches only the upper
+// triangle (diagonal included).
+__device__ void inv_upper_block(float* A, int ms, int r0, int kb, const float* ui) {
+  const int lane = threadIdx.x & 31;
+  float a[32];
+#pragma unroll
+  for (int t = 0; t < 32; ++t) a[t] = (t == lane) ? 1.f : 0.f;
+  float* blk = A + (size_t)r0 * ms + r0;
+  for (int c = 0; c < kb; ++c) {
+    const float x = a[0] * ui[r0 + c];
+    const float* row = blk + (size_t)c * ms + c + 1;  // U_{c, c + 1 + t}
+    float u[32];
+#pragma unroll
+    for (int t = 0; t < 32; ++t) u[t] = c + 1 + t < kb ? row[t] : 0.f;
+    __syncwarp();  // lanes stay in step: entry (r, c) is written after every read of it
+    if (lane <= c && lane < kb) blk[(size_t)lane * ms + c] = x;
+#pragma unroll
+    for (int t = 0; t < 32; ++t) a[t] = fmaf(-x, u[t], t < 31 ? a[t + 1] : 0.f);
+  }
+}
+
+// C = M^{-1} (h + gamma Z) from the factors of k_adapt_lu.  Before the grid dependency wait
+// (the factors come from two launches back, complete once the projection has started) the
+// factors are loaded and the 32 x 32 diagonal blocks of L and U inverted, one warp per block;
+// after it the substitutions run blocked, all threads: y_I = L_II^{-1} b_I, then b_J -= L_JI y_I
+// for the later blocks (and the same backwards with U).  When the factorization was flagged
+// unstable the whole pivoting solve runs instead.
+template <int LP>
+__global__ void __launch_bounds__(256, 1)
+k_small_rhs(const float* __restrict__ K, int ldk, const float* __restrict__ h, int ldh,
+            const float* __restrict__ Z, const float* __restrict__ lgam, float gamma, int L,
+            int lp, int mq, const int* __restrict__ mdev, const float* __restrict__ F, int ldf,
+            const float* __restrict__ luinv, float* __restrict__ C, int* status) {
+  if (__ldcg(mdev + 2)) {
+    rw_grid_wait();
+    rw_grid_trigger();
+    small_solve_body<LP>(K, ldk, h, ldh, Z, lgam, gamma, L, lp, mq, mdev, C, status);
+    return;
+  }
+  extern __shared__ float sm[];
+  const int tid = threadIdx.x, warp = tid >> 5, nw = blockDim.x >> 5;
+  const int m = __ldcg(mdev), ms = m | 1, nt = (m + 31) / 32;
+  float* A = sm;                              // m x ms factors; diagonal blocks inverted
+  float* Y = A + (size_t)m * ms;              // m x LP right-hand sides / solution
+  float* Tt = Y + (size_t)m * LP;             // 32 x LP block in flight
+  __shared__ float ui[kMaxSmallM];
+  // the factors: 16-byte loads (ldf is a multiple of 4), eight per thread in flight
+  const int g4 = (m + 3) / 4, ng = m * g4;
+  for (int e0 = tid; e0 < ng; e0 += 8 * blockDim.x) {
+    float4 v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int e = e0 + u * blockDim.x;
+      v[u] = e < ng ? __ldcg(reinterpret_cast<const float4*>(F + (int64_t)(e / g4) * ldf) + e % g4)
+                    : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int e = e0 + u * blockDim.x;
+      if (e < ng) {
+        const int i = e / g4, j = 4 * (e % g4);
+        float* ar = A + i * ms + j;
+        ar[0] = v[u].x;
+        if (j + 1 < m) ar[1] = v[u].y;
+        if (j + 2 < m) ar[2] = v[u].z;
+        if (j + 3 < m) ar[3] = v[u].w;
+      }
+    }
+  }
+  for (int i = tid; i < m; i += blockDim.x) ui[i] = __ldcg(luinv + i);
+  __syncthreads();
+  // the two triangles of a diagonal block are disjoint: its two inversions run side by side
+  for (int job = warp; job < 2 * nt; job += nw) {
+    const int I = job % nt, r0 = 32 * I, kb = min(32, m - r0);
+    if (job < nt) inv_unit_lower_block(A, ms, r0, kb);
+    else inv_upper_block(A, ms, r0, kb, ui);
+  }
+  __syncthreads();
+  rw_grid_wait();
+  rw_grid_trigger();
+  for (int e = tid; e < m * LP; e += blockDim.x) {
+    const int i = e / LP, k = e % LP;
+    Y[e] = k < L ? fmaf(gamma, Z[(int64_t)i * lp + k], h[(int64_t)i * ldh + k]) : 0.f;
+  }
+  __syncthreads();
+  // forward: y_I = L_II^{-1} b_I, then b_J -= L_J,I y_I below the block
+  for (int I = 0; I < nt; ++I) {
+    const int r0 = 32 * I, kb = min(32, m - r0), r1 = r0 + kb;
+    for (int e = tid; e < kb * LP; e += blockDim.x) {  // unit diagonal
+      const int r = e / LP, k = e % LP;
+      const float* xr = A + (size_t)(r0 + r) * ms + r0;
+      float s = Y[(r0 + r) * LP + k];
+      for (int c = 0; c < r; ++c) s = fmaf(xr[c], Y[(r0 + c) * LP + k], s);
+      Tt[e] = s;
+    }
+    __syncthreads();
+    for (int e = tid; e < kb * LP; e += blockDim.x) Y[r0 * LP + e] = Tt[e];
+    for (int e = tid; e < (m - r1) * LP; e += blockDim.x) {
+      const int j = r1 + e / LP, k = e % LP;
+      const float* lr = A + (size_t)j * ms + r0;
+      float s = Y[j * LP + k];
+      for (int c = 0; c < kb; ++c) s = fmaf(-lr[c], Tt[c * LP + k], s);
+      Y[j * LP + k] = s;
+    }
+    __syncthreads();
+  }
+  // backward: x_I = U_II^{-1} y_I, then y_J -= U_J,I x_I above the block
+  for (int I = nt - 1; I >= 0; --I) {
+    const int r0 = 32 * I, kb = min(32, m - r0);
+    for (int e = tid; e < kb * LP; e += blockDim.x) {
+      const int r = e / LP, k = e % LP;
+      const float* xr = A + (size_t)(r0 + r) * ms + r0;
+      float s = 0.f;
+      for (int c = r; c < kb; ++c) s = fmaf(xr[c], Y[(r0 + c) * LP + k], s);
+      Tt[e] = s;
+    }
+    __syncthreads();
+    for (int e = tid; e < kb * LP; e += blockDim.x) Y[r0 * LP + e] = Tt[e];
+    for (int e = tid; e < r0 * LP; e += blockDim.x) {
+      const int j = e / LP, k = e % LP;
+      const float* ur = A + (size_t)j * ms + r0;
+      float s = Y[j * LP + k];
+      for (int c = 0; c < kb; ++c) s = fmaf(-ur[c], Tt[c * LP + k], s);
+      Y[j * LP + k] = s;
+    }
+    __syncthreads();
+  }
+  for (int e = tid; e < mq * lp; e += blockDim.x) {
+    const int i = e / lp, k = e % lp;
+    C[e] = (i < m && k < L) ? Y[i * LP + k] : 0.f;
+  }
 }
 
 // ---------------------------------------------------------------------------------------
@@ -1953,6 +2576,51 @@ rw_status rw_solve_priors_internal(const rw_graph* g, const int32_t* seed_idx,
                                    int** seedlab_out, double** fit64_out);
 
 // launches k_seed_gram with the seed rows split over a cluster of up to 8 CTAs along z
+// The cluster-fused adaptive choice + LU (k_adapt_lu) when both CTAs' shared memory fits;
+// otherwise the caller runs k_adapt / k_set_m and the one-CTA k_small_solve.
+template <int LP>
+static bool adapt_lu_fits(size_t dyn) {
+  static int optin = -1, stat = -1;
+  if (optin < 0) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+      optin = 0;
+    cudaFuncAttributes fa;
+    stat = cudaFuncGetAttributes(&fa, k_adapt_lu<LP>) == cudaSuccess ? (int)fa.sharedSizeBytes : 1 << 30;
+    cudaGetLastError();
+  }
+  return dyn + (size_t)stat <= (size_t)optin;
+}
+
+template <int LP>
+static rw_status launch_adapt_lu(size_t shm, cudaStream_t st, const float* G, const float* bv,
+                                 const float* Qs, const float* Us, int wcat, int S, int L,
+                                 int m_max, int m_step, double rho, double fmax, int adaptive,
+                                 const float* K, const double* lam, double gamma, float* F,
+                                 int ldf, float* luinv, int* mdev, double* fsel) {
+  RW_CHECK_CUDA(cudaFuncSetAttribute(k_adapt_lu<LP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(2, 1, 1);
+  cfg.blockDim = dim3(256, 1, 1);
+  cfg.dynamicSmemBytes = shm;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[2];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = 2;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[1].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 2;
+  RW_CHECK_CUDA(cudaLaunchKernelEx(&cfg, k_adapt_lu<LP>, G, wcat, bv, wcat, Qs, wcat, Us, wcat, S,
+                                   L, m_max, m_step, rho, fmax, adaptive, K, wcat, lam, gamma, F,
+                                   ldf, luinv, mdev, fsel));
+  rw_count_launch();
+  return RW_OK;
+}
+
 static rw_status seed_gram(const float* A, int lda, const float* B, int ldb, int S, int p, int q,
                            float* G, int ldg, cudaStream_t st) {
   // enough CTAs along z that each holds at most one stage of rows (up to the cluster limit)
@@ -2117,10 +2785,27 @@ extern "C" rw_status rw_solve(const rw_graph* g, const rw_basis* b, const int32_
   double* fu = reinterpret_cast<double*>(P(lay.fu));
   double* fsel = fu + (size_t)(ncand + 1) * RW_MAX_LABELS;
   RW_TRY(mark(2));
-  if (adaptive) {
-    // rho = sqrt(1^T D 1) with the normalized Laplacian (Sec. III-A-1), else sqrt(N)
-    const double rho = g->normalized ? sqrt(g->dsum) : sqrt((double)g->N);
-    const double fmax = (double)S * eps * eps;
+  // rho = sqrt(1^T D 1) with the normalized Laplacian (Sec. III-A-1), else sqrt(N)
+  const double rho = g->normalized ? sqrt(g->dsum) : sqrt((double)g->N);
+  const double fmax = (double)S * eps * eps;
+  float* Fac = reinterpret_cast<float*>(P(lay.lu));
+  float* luinv = reinterpret_cast<float*>(P(lay.luinv));
+  const size_t shm_fused =
+      sizeof(float) * std::max((size_t)m_max * (m_max | 1) + 3 * (size_t)L * m_max,
+                               (size_t)m_max * lu_stride(m_max) + (size_t)kLuTiles * m_max);
+  const bool fused = lp == 4 ? adapt_lu_fits<4>(shm_fused)
+                             : (lp == 8 ? adapt_lu_fits<8>(shm_fused) : adapt_lu_fits<16>(shm_fused));
+  if (fused) {
+    if (lp == 4)
+      RW_TRY(launch_adapt_lu<4>(shm_fused, st, G, bv, Qs, Us, wcat, S, L, m_max, m_step, rho, fmax,
+                                adaptive, K, b->lam, gamma, Fac, mp, luinv, mdev, fsel));
+    else if (lp == 8)
+      RW_TRY(launch_adapt_lu<8>(shm_fused, st, G, bv, Qs, Us, wcat, S, L, m_max, m_step, rho, fmax,
+                                adaptive, K, b->lam, gamma, Fac, mp, luinv, mdev, fsel));
+    else
+      RW_TRY(launch_adapt_lu<16>(shm_fused, st, G, bv, Qs, Us, wcat, S, L, m_max, m_step, rho,
+                                 fmax, adaptive, K, b->lam, gamma, Fac, mp, luinv, mdev, fsel));
+  } else if (adaptive) {
     const size_t shm = sizeof(float) * ((size_t)m_max * (m_max | 1) + 3 * (size_t)L * m_max);
     if (lp == 4) {
       cudaFuncSetAttribute(k_adapt<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
@@ -2172,7 +2857,23 @@ extern "C" rw_status rw_solve(const rw_graph* g, const rw_basis* b, const int32_
   {
     size_t shm = sizeof(float) * ((size_t)m_max * ((m_max + L) | 1) + 2 * (size_t)L * m_max + m_max) +
                  sizeof(int) * m_max;
-    if (lp == 4) {
+    if (fused)  // the factors, the right-hand sides and one block of them
+      shm = std::max(shm, sizeof(float) * ((size_t)m_max * (m_max | 1) + (size_t)(m_max + 32) * lp));
+    if (fused) {
+      if (lp == 4) {
+        cudaFuncSetAttribute(k_small_rhs<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+        RW_LAUNCH((k_small_rhs<4>), 1, 256, shm, st, K, wcat, h, wcat, Z, lgam, (float)gamma, L, lp, mq,
+                  mdev, Fac, mp, luinv, C, g->status);
+      } else if (lp == 8) {
+        cudaFuncSetAttribute(k_small_rhs<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+        RW_LAUNCH((k_small_rhs<8>), 1, 256, shm, st, K, wcat, h, wcat, Z, lgam, (float)gamma, L, lp, mq,
+                  mdev, Fac, mp, luinv, C, g->status);
+      } else {
+        cudaFuncSetAttribute(k_small_rhs<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+        RW_LAUNCH((k_small_rhs<16>), 1, 256, shm, st, K, wcat, h, wcat, Z, lgam, (float)gamma, L, lp, mq,
+                  mdev, Fac, mp, luinv, C, g->status);
+      }
+    } else if (lp == 4) {
       cudaFuncSetAttribute(k_small_solve<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
       RW_LAUNCH((k_small_solve<4>), 1, 256, shm, st, K, wcat, h, wcat, Z, lgam, (float)gamma, L, lp, mq, mdev, C,
                                             g->status);
