@@ -506,9 +506,10 @@ __device__ void chol_diag_rot(float* A, int ms, int k0, int kb, float* dinv, flo
     a[c] = v;
   }
   for (int kk = 0; kk < kb; ++kk) {
+    // every lane stores: a_lane,kk below the pivot at [lane - kk - 1], the pivot at [32], lanes
+    // above it into the unused slots [33 + lane]
     float* b = buf + 64 * (kk & 1);
-    if (lane > kk) b[lane - kk - 1] = a[0];  // a_lane,kk below the pivot
-    else if (lane == kk) b[32] = a[0];       // pivot
+    b[lane > kk ? lane - kk - 1 : (lane == kk ? 32 : 33 + lane)] = a[0];
     __syncwarp();
     float d = b[32];
     float4 v[8];
@@ -519,11 +520,10 @@ __device__ void chol_diag_rot(float* A, int ms, int k0, int kb, float* dinv, flo
     }
     const float f = __fdividef(a[0], d);
     const float ri = rsqrtf(d);
-    if (live && lane > kk) row[kk] = a[0] * ri;  // L_lane,kk
-    if (lane == kk) {
-      row[kk] = d * ri;                          // L_kk = sqrt(d)
-      dinv[kk] = ri;
-    }
+    // L_lane,kk = a_lane,kk / sqrt(d) (the pivot lane writes sqrt(d)); lanes above the pivot
+    // write into the block's unused upper triangle
+    if (live) row[kk] = a[0] * ri;
+    if (lane == kk) dinv[kk] = ri;
     shift_update_r(a, f, v);
   }
   __syncwarp();
@@ -1183,14 +1183,17 @@ __device__ void adapt_body(const float* __restrict__ G, int ldg, const float* __
     }
     __syncthreads();
     rows_done = r0 + nr;
-    if (tid == 0) {
-      for (int c = 0; c < ncand && chosen < 0; ++c) {
-        const int m = cand_m(c);
-        if (m <= r0 || m > r0 + nr) continue;
-        bool pass = !bad;
-        for (int k = 0; k < L; ++k)
+    if (warp == 0) {  // the first candidate inside this tile that passes for every label
+      for (int cb = 0; cb < ncand; cb += 32) {
+        const int c = cb + lane, m = cand_m(c);
+        bool pass = c < ncand && m > r0 && m <= r0 + nr && !bad;
+        for (int k = 0; k < L && pass; ++k)
           if (!(al[k * mmax + c] <= (float)fmax)) pass = false;
-        if (pass) chosen = c;
+        const unsigned bal = __ballot_sync(0xffffffff, pass);
+        if (bal) {
+          if (lane == 0) chosen = cb + __ffs(bal) - 1;
+          break;
+        }
       }
     }
     __syncthreads();
@@ -1924,34 +1927,17 @@ k_small_rhs(const float* __restrict__ K, int ldk, const float* __restrict__ h, i
   }
   extern __shared__ float sm[];
   const int tid = threadIdx.x, warp = tid >> 5, nw = blockDim.x >> 5;
-  const int m = __ldcg(mdev), ms = m | 1, nt = (m + 31) / 32;
+  const int m = __ldcg(mdev), ms = lu_stride(m), nt = (m + 31) / 32;
   float* A = sm;                              // m x ms factors; diagonal blocks inverted
   float* Y = A + (size_t)m * ms;              // m x LP right-hand sides / solution
   float* Tt = Y + (size_t)m * LP;             // 32 x LP block in flight
   __shared__ float ui[kMaxSmallM];
-  // the factors: 16-byte loads (ldf is a multiple of 4), eight per thread in flight
-  const int g4 = (m + 3) / 4, ng = m * g4;
-  for (int e0 = tid; e0 < ng; e0 += 8 * blockDim.x) {
-    float4 v[8];
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const int e = e0 + u * blockDim.x;
-      v[u] = e < ng ? __ldcg(reinterpret_cast<const float4*>(F + (int64_t)(e / g4) * ldf) + e % g4)
-                    : make_float4(0.f, 0.f, 0.f, 0.f);
-    }
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const int e = e0 + u * blockDim.x;
-      if (e < ng) {
-        const int i = e / g4, j = 4 * (e % g4);
-        float* ar = A + i * ms + j;
-        ar[0] = v[u].x;
-        if (j + 1 < m) ar[1] = v[u].y;
-        if (j + 2 < m) ar[2] = v[u].z;
-        if (j + 3 < m) ar[3] = v[u].w;
-      }
-    }
-  }
+  // the factors: every 16-byte piece requested at once (ldf and ms are multiples of 4; whole
+  // pieces past column m are copied and never read)
+  const int g4 = (m + 3) / 4;
+  for (int i = warp; i < m; i += nw)
+    for (int c = tid & 31; c < g4; c += 32) cp_async16(A + (size_t)i * ms + 4 * c, F + (int64_t)i * ldf + 4 * c);
+  cp_async_wait_all();
   for (int i = tid; i < m; i += blockDim.x) ui[i] = __ldcg(luinv + i);
   __syncthreads();
   // the two triangles of a diagonal block are disjoint: its two inversions run side by side
@@ -2858,7 +2844,7 @@ extern "C" rw_status rw_solve(const rw_graph* g, const rw_basis* b, const int32_
     size_t shm = sizeof(float) * ((size_t)m_max * ((m_max + L) | 1) + 2 * (size_t)L * m_max + m_max) +
                  sizeof(int) * m_max;
     if (fused)  // the factors, the right-hand sides and one block of them
-      shm = std::max(shm, sizeof(float) * ((size_t)m_max * (m_max | 1) + (size_t)(m_max + 32) * lp));
+      shm = std::max(shm, sizeof(float) * ((size_t)m_max * lu_stride(m_max) + (size_t)(m_max + 32) * lp));
     if (fused) {
       if (lp == 4) {
         cudaFuncSetAttribute(k_small_rhs<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
