@@ -184,40 +184,71 @@ k_priors(const float* __restrict__ J, const float* __restrict__ sq, int64_t N, i
   else if (blockIdx.x == 0)
     seed_fit(bpart, nsb, L, prior_mode, fit, fit64, nullptr);
   __syncthreads();
-  // grid-stride over the voxels (a few waves of blocks, so the fit above is amortized)
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    float p[LP];
-    if (prior_mode == 0) {
-      const float x = J[i];
-      float mx = -INFINITY;
-#pragma unroll
-      for (int k = 0; k < LP; ++k) {
-        const float t = x - fit[k];
-        p[k] = (k < L) ? -t * t * fit[16 + k] - fit[32 + k] : -INFINITY;
-        mx = fmaxf(mx, p[k]);
-      }
-      float sum = 0.f;
-#pragma unroll
-      for (int k = 0; k < LP; ++k) {
-        p[k] = (k < L) ? __expf(p[k] - mx) : 0.f;
-        sum += p[k];
-      }
-      const float inv = 1.f / sum;
-#pragma unroll
-      for (int k = 0; k < LP; ++k) p[k] *= inv;
+  // grid-stride over groups of four consecutive voxels (16-byte loads of J and d^{1/2}, all of
+  // a group's loads issued together; a few waves of blocks, so the fit above is amortized)
+  const int64_t ng = (N + 3) / 4;
+  for (int64_t gI = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; gI < ng;
+       gI += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i0 = 4 * gI;
+    const bool full = i0 + 3 < N;
+    float xv[4] = {0.f, 0.f, 0.f, 0.f}, rv[4] = {0.f, 0.f, 0.f, 0.f};
+    float pin[4][LP];
+    if (full) {
+      const float4 r4 = *reinterpret_cast<const float4*>(sq + i0);
+      rv[0] = r4.x; rv[1] = r4.y; rv[2] = r4.z; rv[3] = r4.w;
     } else {
 #pragma unroll
-      for (int k = 0; k < LP; ++k) {
-        p[k] = (k < L) ? Pin[i * L + k] : 0.f;
-        if (k < L && !isfinite(p[k])) atomicOr(status, RW_DEV_NONFINITE);
-      }
+      for (int u = 0; u < 4; ++u) rv[u] = i0 + u < N ? sq[i0 + u] : 0.f;
     }
-    const float r = sq[i];
-    float4* o = reinterpret_cast<float4*>(phat + i * LP);
+    if (prior_mode == 0) {
+      if (full) {
+        const float4 j4 = *reinterpret_cast<const float4*>(J + i0);
+        xv[0] = j4.x; xv[1] = j4.y; xv[2] = j4.z; xv[3] = j4.w;
+      } else {
 #pragma unroll
-    for (int k4 = 0; k4 < LP / 4; ++k4)
-      o[k4] = make_float4(r * p[4 * k4], r * p[4 * k4 + 1], r * p[4 * k4 + 2], r * p[4 * k4 + 3]);
+        for (int u = 0; u < 4; ++u) xv[u] = i0 + u < N ? J[i0 + u] : 0.f;
+      }
+    } else {
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int k = 0; k < LP; ++k) pin[u][k] = (k < L && i0 + u < N) ? Pin[(i0 + u) * L + k] : 0.f;
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int64_t i = i0 + u;
+      if (i >= N) break;
+      float p[LP];
+      if (prior_mode == 0) {
+        float mx = -INFINITY;
+#pragma unroll
+        for (int k = 0; k < LP; ++k) {
+          const float t = xv[u] - fit[k];
+          p[k] = (k < L) ? -t * t * fit[16 + k] - fit[32 + k] : -INFINITY;
+          mx = fmaxf(mx, p[k]);
+        }
+        float sum = 0.f;
+#pragma unroll
+        for (int k = 0; k < LP; ++k) {
+          p[k] = (k < L) ? __expf(p[k] - mx) : 0.f;
+          sum += p[k];
+        }
+        const float inv = 1.f / sum;
+#pragma unroll
+        for (int k = 0; k < LP; ++k) p[k] *= inv;
+      } else {
+#pragma unroll
+        for (int k = 0; k < LP; ++k) {
+          p[k] = pin[u][k];
+          if (k < L && !isfinite(p[k])) atomicOr(status, RW_DEV_NONFINITE);
+        }
+      }
+      float4* o = reinterpret_cast<float4*>(phat + i * LP);
+#pragma unroll
+      for (int k4 = 0; k4 < LP / 4; ++k4)
+        o[k4] = make_float4(rv[u] * p[4 * k4], rv[u] * p[4 * k4 + 1], rv[u] * p[4 * k4 + 2],
+                            rv[u] * p[4 * k4 + 3]);
+    }
   }
 }
 
@@ -1123,14 +1154,16 @@ __device__ void adapt_body(const float* __restrict__ G, int ldg, const float* __
           if (r < r0 + nr) y[q] = fmaf(-A[r * ms + t], l, y[q]);
         }
       }
-      for (int u = 0; u < 32; ++u) {
+      const float* lrow_j = A + (c0 + lane) * ms + c0;  // row c0 + lane of block J
+      for (int u = 0; u < 32; ++u) {  // branch-free: loads for every lane, selects below
         const float du = dinv[c0 + u];
-        const float lu = (lane > u) ? A[(c0 + lane) * ms + c0 + u] : 0.f;
+        const float lu = lrow_j[u];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-          if (lane == u) y[q] *= du;
+          y[q] = lane == u ? y[q] * du : y[q];
           const float xu = __shfl_sync(0xffffffff, y[q], u);
-          if (lane > u) y[q] = fmaf(-xu, lu, y[q]);
+          const float yn = fmaf(-xu, lu, y[q]);
+          y[q] = lane > u ? yn : y[q];
         }
       }
 #pragma unroll
@@ -1159,10 +1192,14 @@ __device__ void adapt_body(const float* __restrict__ G, int ldg, const float* __
         y = bb[k * mmax + r0 + lane];
         for (int t = 0; t < r0; ++t) y = fmaf(-A[(r0 + lane) * ms + t], z[k * mmax + t], y);
       }
-      for (int u = 0; u < nr; ++u) {
-        if (lane == u) y *= dinv[r0 + u];
+      const float* zrow = A + (r0 + (lane < nr ? lane : 0)) * ms + r0;
+      for (int u = 0; u < nr; ++u) {  // branch-free: loads for every lane, selects below
+        const float du = dinv[r0 + u];
+        const float a = zrow[u];
+        y = lane == u ? y * du : y;
         const float zu = __shfl_sync(0xffffffff, y, u);
-        if (lane > u && lane < nr) y = fmaf(-zu, A[(r0 + lane) * ms + r0 + u], y);
+        const float yn = fmaf(-zu, a, y);
+        y = (lane > u && lane < nr) ? yn : y;
       }
       if (lane < nr) z[k * mmax + r0 + lane] = y;
       // prefix sums of z^2 inside the tile; f_u(m) = ck - zz - prefix
@@ -1859,60 +1896,12 @@ k_adapt_lu(const float* __restrict__ G, int ldg, const float* __restrict__ bv, i
   }
 }
 
-// In place, the inverse of the unit-lower diagonal block of A at (r0, r0) (kb x kb), one warp:
-// lane c solves L x = e_c with the column shifted through registers and writes the strictly lower
-// entries of (L^{-1}) over L (entries of L are read one step before their row is written).
-// Touches only the strictly lower triangle of the block.
-__device__ void inv_unit_lower_block(float* A, int ms, int r0, int kb) {
-  const int lane = threadIdx.x & 31;
-  float a[32];
-#pragma unroll
-  for (int t = 0; t < 32; ++t) a[t] = (t == lane) ? 1.f : 0.f;
-  float* blk = A + (size_t)r0 * ms + r0;
-  for (int r = 0; r < kb; ++r) {
-    const float y = a[0];
-    float l[32];
-#pragma unroll
-    for (int t = 0; t < 32; ++t) {
-      const int rr = r + 1 + t;
-      l[t] = rr < kb ? blk[(size_t)rr * ms + r] : 0.f;  // L_{r + 1 + t, r}
-    }
-    __syncwarp();  // lanes stay in step: entry (r, c) is written after every read of it
-    if (lane < r) blk[(size_t)r * ms + lane] = y;
-#pragma unroll
-    for (int t = 0; t < 32; ++t) a[t] = fmaf(-y, l[t], t < 31 ? a[t + 1] : 0.f);
-  }
-}
-
-// In place, the inverse of the upper diagonal block (reciprocal diagonal in ui): lane r solves
-// x U = e_r with the row shifted through registers and writes (U^{-1})_rc for c >= r over U
-// (row c of U is read before any entry of column c is written).  Touches only the upper
-// triangle (diagonal included).
-__device__ void inv_upper_block(float* A, int ms, int r0, int kb, const float* ui) {
-  const int lane = threadIdx.x & 31;
-  float a[32];
-#pragma unroll
-  for (int t = 0; t < 32; ++t) a[t] = (t == lane) ? 1.f : 0.f;
-  float* blk = A + (size_t)r0 * ms + r0;
-  for (int c = 0; c < kb; ++c) {
-    const float x = a[0] * ui[r0 + c];
-    const float* row = blk + (size_t)c * ms + c + 1;  // U_{c, c + 1 + t}
-    float u[32];
-#pragma unroll
-    for (int t = 0; t < 32; ++t) u[t] = c + 1 + t < kb ? row[t] : 0.f;
-    __syncwarp();  // lanes stay in step: entry (r, c) is written after every read of it
-    if (lane <= c && lane < kb) blk[(size_t)lane * ms + c] = x;
-#pragma unroll
-    for (int t = 0; t < 32; ++t) a[t] = fmaf(-x, u[t], t < 31 ? a[t + 1] : 0.f);
-  }
-}
-
 // C = M^{-1} (h + gamma Z) from the factors of k_adapt_lu.  Before the grid dependency wait
 // (the factors come from two launches back, complete once the projection has started) the
-// factors are loaded and the 32 x 32 diagonal blocks of L and U inverted, one warp per block;
-// after it the substitutions run blocked, all threads: y_I = L_II^{-1} b_I, then b_J -= L_JI y_I
-// for the later blocks (and the same backwards with U).  When the factorization was flagged
-// unstable the whole pivoting solve runs instead.
+// factors are copied in; after it the substitutions run by 32-row blocks: one warp solves the
+// diagonal block for all labels (lane = row, labels in registers), then all threads update the
+// remaining rows.  When the factorization was flagged unstable the whole pivoting solve runs
+// instead.
 template <int LP>
 __global__ void __launch_bounds__(256, 1)
 k_small_rhs(const float* __restrict__ K, int ldk, const float* __restrict__ h, int ldh,
@@ -1928,9 +1917,8 @@ k_small_rhs(const float* __restrict__ K, int ldk, const float* __restrict__ h, i
   extern __shared__ float sm[];
   const int tid = threadIdx.x, warp = tid >> 5, nw = blockDim.x >> 5;
   const int m = __ldcg(mdev), ms = lu_stride(m), nt = (m + 31) / 32;
-  float* A = sm;                              // m x ms factors; diagonal blocks inverted
-  float* Y = A + (size_t)m * ms;              // m x LP right-hand sides / solution
-  float* Tt = Y + (size_t)m * LP;             // 32 x LP block in flight
+  float* A = sm;                              // m x ms factors
+  float* Y = A + (size_t)m * ms;              // LP x m right-hand sides / solution (label-major)
   __shared__ float ui[kMaxSmallM];
   // the factors: every 16-byte piece requested at once (ldf and ms are multiples of 4; whole
   // pieces past column m are copied and never read)
@@ -1940,65 +1928,73 @@ k_small_rhs(const float* __restrict__ K, int ldk, const float* __restrict__ h, i
   cp_async_wait_all();
   for (int i = tid; i < m; i += blockDim.x) ui[i] = __ldcg(luinv + i);
   __syncthreads();
-  // the two triangles of a diagonal block are disjoint: its two inversions run side by side
-  for (int job = warp; job < 2 * nt; job += nw) {
-    const int I = job % nt, r0 = 32 * I, kb = min(32, m - r0);
-    if (job < nt) inv_unit_lower_block(A, ms, r0, kb);
-    else inv_upper_block(A, ms, r0, kb, ui);
-  }
-  __syncthreads();
   rw_grid_wait();
   rw_grid_trigger();
-  for (int e = tid; e < m * LP; e += blockDim.x) {
-    const int i = e / LP, k = e % LP;
-    Y[e] = k < L ? fmaf(gamma, Z[(int64_t)i * lp + k], h[(int64_t)i * ldh + k]) : 0.f;
+  // one warp per label, independent of the others: its vector y (label-major in Y) is solved by
+  // 32-row blocks: the diagonal block by a chain over the lanes (lane = row, one shuffle per
+  // step), then the rows past it (forward) or before it (backward) by the block's product
+  const int lane = tid & 31;
+  for (int k = warp; k < L; k += nw) {
+    float* y = Y + (size_t)k * m;
+    for (int i = lane; i < m; i += 32) y[i] = fmaf(gamma, Z[(int64_t)i * lp + k], h[(int64_t)i * ldh + k]);
+    __syncwarp();
+    for (int I = 0; I < nt; ++I) {  // L y = b, L unit lower
+      const int r0 = 32 * I, kb = min(32, m - r0), r1 = r0 + kb;
+      const bool live = lane < kb;
+      const float* lr = A + (size_t)(r0 + (live ? lane : 0)) * ms + r0;
+      float yi = live ? y[r0 + lane] : 0.f;
+      for (int c = 0; c < kb; ++c) {
+        const float lc = lr[c];  // inside the row for every lane; used below the diagonal only
+        const float yn = fmaf(-lc, __shfl_sync(0xffffffff, yi, c), yi);
+        yi = lane > c ? yn : yi;
+      }
+      if (live) y[r0 + lane] = yi;
+      __syncwarp();
+      for (int j = r1 + lane; j < m; j += 32) {
+        const float* ar = A + (size_t)j * ms + r0;
+        float s0 = y[j], s1 = 0.f;
+        int c = 0;
+        for (; c + 1 < kb; c += 2) {
+          s0 = fmaf(-ar[c], y[r0 + c], s0);
+          s1 = fmaf(-ar[c + 1], y[r0 + c + 1], s1);
+        }
+        if (c < kb) s0 = fmaf(-ar[c], y[r0 + c], s0);
+        y[j] = s0 + s1;
+      }
+      __syncwarp();
+    }
+    for (int I = nt - 1; I >= 0; --I) {  // U x = y, 1 / U_ii in ui
+      const int r0 = 32 * I, kb = min(32, m - r0);
+      const bool live = lane < kb;
+      const float* ur = A + (size_t)(r0 + (live ? lane : 0)) * ms + r0;
+      const float uii = live ? ui[r0 + lane] : 0.f;
+      float yi = live ? y[r0 + lane] : 0.f;
+      for (int c = kb - 1; c >= 0; --c) {
+        const float uc = ur[c];  // inside the row for every lane; used above the diagonal only
+        const float xc = __shfl_sync(0xffffffff, yi * uii, c);
+        const float yn = fmaf(-uc, xc, yi);
+        yi = lane == c ? xc : (lane < c ? yn : yi);
+      }
+      if (live) y[r0 + lane] = yi;
+      __syncwarp();
+      for (int j = lane; j < r0; j += 32) {
+        const float* ar = A + (size_t)j * ms + r0;
+        float s0 = y[j], s1 = 0.f;
+        int c = 0;
+        for (; c + 1 < kb; c += 2) {
+          s0 = fmaf(-ar[c], y[r0 + c], s0);
+          s1 = fmaf(-ar[c + 1], y[r0 + c + 1], s1);
+        }
+        if (c < kb) s0 = fmaf(-ar[c], y[r0 + c], s0);
+        y[j] = s0 + s1;
+      }
+      __syncwarp();
+    }
   }
   __syncthreads();
-  // forward: y_I = L_II^{-1} b_I, then b_J -= L_J,I y_I below the block
-  for (int I = 0; I < nt; ++I) {
-    const int r0 = 32 * I, kb = min(32, m - r0), r1 = r0 + kb;
-    for (int e = tid; e < kb * LP; e += blockDim.x) {  // unit diagonal
-      const int r = e / LP, k = e % LP;
-      const float* xr = A + (size_t)(r0 + r) * ms + r0;
-      float s = Y[(r0 + r) * LP + k];
-      for (int c = 0; c < r; ++c) s = fmaf(xr[c], Y[(r0 + c) * LP + k], s);
-      Tt[e] = s;
-    }
-    __syncthreads();
-    for (int e = tid; e < kb * LP; e += blockDim.x) Y[r0 * LP + e] = Tt[e];
-    for (int e = tid; e < (m - r1) * LP; e += blockDim.x) {
-      const int j = r1 + e / LP, k = e % LP;
-      const float* lr = A + (size_t)j * ms + r0;
-      float s = Y[j * LP + k];
-      for (int c = 0; c < kb; ++c) s = fmaf(-lr[c], Tt[c * LP + k], s);
-      Y[j * LP + k] = s;
-    }
-    __syncthreads();
-  }
-  // backward: x_I = U_II^{-1} y_I, then y_J -= U_J,I x_I above the block
-  for (int I = nt - 1; I >= 0; --I) {
-    const int r0 = 32 * I, kb = min(32, m - r0);
-    for (int e = tid; e < kb * LP; e += blockDim.x) {
-      const int r = e / LP, k = e % LP;
-      const float* xr = A + (size_t)(r0 + r) * ms + r0;
-      float s = 0.f;
-      for (int c = r; c < kb; ++c) s = fmaf(xr[c], Y[(r0 + c) * LP + k], s);
-      Tt[e] = s;
-    }
-    __syncthreads();
-    for (int e = tid; e < kb * LP; e += blockDim.x) Y[r0 * LP + e] = Tt[e];
-    for (int e = tid; e < r0 * LP; e += blockDim.x) {
-      const int j = e / LP, k = e % LP;
-      const float* ur = A + (size_t)j * ms + r0;
-      float s = Y[j * LP + k];
-      for (int c = 0; c < kb; ++c) s = fmaf(-ur[c], Tt[c * LP + k], s);
-      Y[j * LP + k] = s;
-    }
-    __syncthreads();
-  }
   for (int e = tid; e < mq * lp; e += blockDim.x) {
     const int i = e / lp, k = e % lp;
-    C[e] = (i < m && k < L) ? Y[i * LP + k] : 0.f;
+    C[e] = (i < m && k < L) ? Y[(size_t)k * m + i] : 0.f;
   }
 }
 
@@ -2658,7 +2654,7 @@ rw_status rw_solve_priors_internal(const rw_graph* g, const int32_t* seed_idx,
     RW_LAUNCH(k_seed_reset, rw_blocks(g->N, 256), 256, 0, st, seedlab, g->N, nullptr, 0);
   ws.seeds_clean = false;
   const int sms = g_rw_num_sms > 0 ? g_rw_num_sms : 148;
-  const int pblk = (int)std::min<int64_t>(rw_blocks(g->N, 256), 8 * sms);
+  const int pblk = (int)std::min<int64_t>(rw_blocks((g->N + 3) / 4, 256), 8 * sms);
   RW_LAUNCH(k_seed_scatter, nsb, 256, 0, st, seed_idx, seed_lab, S, L, g->N,
             g->J ? g->J : nullptr, seedlab, bpart, g->status);
   if (lp == 4)
