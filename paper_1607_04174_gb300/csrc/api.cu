@@ -39,6 +39,7 @@ rw_status rw_status_from_device_bits(int bits) {
   if (bits & RW_DEV_NONFINITE) return RW_ERR_INVALID_ARG;
   if (bits & RW_DEV_ISOLATED) return RW_ERR_ISOLATED_NODE;
   if (bits & RW_DEV_SINGULAR) return RW_ERR_SINGULAR;
+  if (bits & RW_DEV_TIMEOUT) return RW_ERR_TIMEOUT;
   return RW_OK;
 }
 

@@ -70,7 +70,8 @@ enum : int {
   RW_DEV_ISOLATED = 4,       // degree 0 with the normalized Laplacian
   RW_DEV_SINGULAR = 8,       // zero pivot in a small dense factorization
   RW_DEV_EMPTY_LABEL = 16,   // a label without seeds (Gaussian priors need one)
-  RW_DEV_NONFINITE = 32      // NaN / Inf in an input
+  RW_DEV_NONFINITE = 32,     // NaN / Inf in an input
+  RW_DEV_TIMEOUT = 64        // a bounded wait on an asynchronous copy gave up
 };
 rw_status rw_status_from_device_bits(int bits);
 

@@ -76,6 +76,35 @@ __device__ __forceinline__ void cp_async16(float* dst, const float* src) {
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
+// mbarrier + bulk asynchronous copy (global -> shared, completion counted in bytes on the
+// barrier).  Waits are bounded: a wait that gives up sets RW_DEV_TIMEOUT.
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
+               :: "r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+               :: "r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+               " selp.u32 %0, 1, 0, p;\n}" : "=r"(ok) : "r"(smem_u32(bar)), "r"(parity) : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ void mbar_wait_bounded(uint64_t* bar, unsigned parity, int* status) {
+  for (int it = 0; !mbar_try_wait(bar, parity); ++it) {
+    if (it > (1 << 24)) {
+      if (status) atomicOr(status, RW_DEV_TIMEOUT);
+      return;
+    }
+  }
+}
+
 // ---------------------------------------------------------------------------------------
 __global__ void k_seed_reset(int* __restrict__ seedlab, int64_t n, double* __restrict__ stats,
                              int nstats) {
@@ -2206,6 +2235,109 @@ k_project_cw(const T* __restrict__ Qp, int64_t N, int nchunk_max, const float* _
 
 // U-hat_n = Q_n C on the panel layout: lane = row, the chunk's 8 x LP coefficients come from
 // shared memory as broadcasts; no cross-lane reduction.
+// Z partials with the basis streamed through shared memory by bulk asynchronous copies: a
+// block owns a range of rows, taken in tiles of kPtRows rows; for each tile the masked priors
+// of a thread's rows are loaded once (registers) and the tile's 16-byte rows of every
+// chunk arrive in a kPtStages-deep ring (one bulk copy per (tile, chunk), completion on an
+// mbarrier).  Per step a thread forms its rows' 8 x LP products, a reduce-scatter butterfly
+// sums them over the warp and the warp adds them to its own accumulator (step order: fixed);
+// the warps are added in order at the end.  Block partials as k_project_cw writes them.
+constexpr int kPtRows = 1024, kPtStages = 4, kPtRowsPerThread = kPtRows / 256;
+
+template <typename T, int LP>
+__global__ void __launch_bounds__(256, 2)
+k_project_tma(const T* __restrict__ Qp, int64_t N, int nchunk_max, const float* __restrict__ phat,
+              const int* __restrict__ seedlab, const int* __restrict__ mdev,
+              int64_t rows_per_block, float* __restrict__ part, int* status) {
+  rw_grid_wait();
+  rw_grid_trigger();
+  constexpr int NV = 8 * LP, NG = NV / 32;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  uint4* stage = reinterpret_cast<uint4*>(smraw);                      // kPtStages x kPtRows
+  float* red = reinterpret_cast<float*>(stage + kPtStages * kPtRows);  // nw x nchunk_max x NV
+  __shared__ __align__(8) uint64_t bar[kPtStages];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  const int m = mdev[0];
+  const int nch = min((m + 7) / 8, nchunk_max);
+  const int64_t r0 = (int64_t)blockIdx.x * rows_per_block;
+  const int64_t r1 = min(N, r0 + rows_per_block);
+  const int ntile = r1 > r0 ? (int)((r1 - r0 + kPtRows - 1) / kPtRows) : 0;
+  const int nsteps = ntile * nch;
+  float* wred = red + (size_t)warp * nchunk_max * NV;
+  for (int e = lane; e < nchunk_max * NV; e += 32) wred[e] = 0.f;
+  if (tid == 0)
+    for (int s = 0; s < kPtStages; ++s) mbar_init(&bar[s], 1);
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  __syncthreads();
+  auto issue = [&](int q) {  // step q = (tile q / nch, chunk q % nch) into stage q % kPtStages
+    const int t = q / nch, c = q % nch;
+    const int64_t i0 = r0 + (int64_t)t * kPtRows;
+    const unsigned bytes = (unsigned)(min((int64_t)kPtRows, r1 - i0) * 16);
+    uint64_t* b = &bar[q % kPtStages];
+    mbar_expect_tx(b, bytes);
+    bulk_g2s(stage + (q % kPtStages) * kPtRows, Qp + ((int64_t)c * N + i0) * 8, bytes, b);
+  };
+  if (tid == 0)
+    for (int q = 0; q < min(kPtStages, nsteps); ++q) issue(q);
+  float p[kPtRowsPerThread][LP];
+  for (int q = 0; q < nsteps; ++q) {
+    const int t = q / nch, c = q % nch;
+    const int64_t i0 = r0 + (int64_t)t * kPtRows;
+    const int rows = (int)min((int64_t)kPtRows, r1 - i0);
+    if (c == 0) {  // the tile's priors, seeds masked, for rows tid + 256 u
+#pragma unroll
+      for (int u = 0; u < kPtRowsPerThread; ++u) {
+        const int r = tid + 256 * u;
+        const bool use = r < rows && __ldg(seedlab + i0 + r) < 0;
+#pragma unroll
+        for (int k4 = 0; k4 < LP / 4; ++k4) {
+          const float4 v = r < rows ? __ldg(reinterpret_cast<const float4*>(phat + (i0 + r) * LP) + k4)
+                                    : make_float4(0.f, 0.f, 0.f, 0.f);
+          p[u][4 * k4 + 0] = use ? v.x : 0.f;
+          p[u][4 * k4 + 1] = use ? v.y : 0.f;
+          p[u][4 * k4 + 2] = use ? v.z : 0.f;
+          p[u][4 * k4 + 3] = use ? v.w : 0.f;
+        }
+      }
+    }
+    mbar_wait_bounded(&bar[q % kPtStages], (unsigned)((q / kPtStages) & 1), status);
+    const uint4* sq = stage + (q % kPtStages) * kPtRows;
+    float acc[NV];
+#pragma unroll
+    for (int j = 0; j < NV; ++j) acc[j] = 0.f;
+#pragma unroll
+    for (int u = 0; u < kPtRowsPerThread; ++u) {
+      const int r = tid + 256 * u;
+      if (r < rows) {
+        float qv[8];
+        Vec16<T>::unpack(sq[r], qv);
+#pragma unroll
+        for (int v = 0; v < 8; ++v)
+#pragma unroll
+          for (int k = 0; k < LP; ++k) acc[v * LP + k] = fmaf(qv[v], p[u][k], acc[v * LP + k]);
+      }
+    }
+#pragma unroll
+    for (int gq = 0; gq < NG; ++gq) {
+      float val[32];
+#pragma unroll
+      for (int j = 0; j < 32; ++j) val[j] = acc[32 * gq + j];
+      const float sum = reduce_scatter32(val, lane);  // lane j: product 32 gq + j
+      wred[c * NV + 32 * gq + lane] += sum;
+    }
+    __syncthreads();  // stage q % kPtStages consumed
+    if (tid == 0 && q + kPtStages < nsteps) issue(q + kPtStages);
+  }
+  __syncthreads();
+  float* pb = part + (int64_t)blockIdx.x * nchunk_max * NV;
+  for (int e = tid; e < nchunk_max * NV; e += blockDim.x) {
+    float v = 0.f;
+    if (e / NV < nch)
+      for (int w = 0; w < nw; ++w) v += red[(size_t)w * nchunk_max * NV + e];
+    pb[e] = v;
+  }
+}
+
 constexpr int kBackChunks = 8;  // 16-byte chunks per row in flight in the back-projection
 
 template <typename T, int LP>
@@ -2492,12 +2624,19 @@ rw_status launch_proj_back(bool back, const T* Q, int ldq, const float* phat,
   if constexpr (V == 8) {  // 16-bit copies: panel-major layout, ldq = 8 x chunks
     const int nchunk = ldq / 8;
     if (!back) {
-      const size_t shm = sizeof(float) * kParts * (size_t)nchunk * 8 * LP;
-      if (shm > 48 * 1024)
-        cudaFuncSetAttribute(k_project_cw<T, LP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
       const int64_t rpb = (g->N + nblk - 1) / nblk;
-      RW_LAUNCH((k_project_cw<T, LP>), nblk, 256, shm, st, Q, g->N, nchunk, phat, seedlab, mdev,
-                rpb, part);
+      if constexpr (LP <= 8) {
+        const size_t shm = sizeof(uint4) * kPtStages * kPtRows + sizeof(float) * 8 * (size_t)nchunk * 8 * LP;
+        cudaFuncSetAttribute(k_project_tma<T, LP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+        RW_LAUNCH((k_project_tma<T, LP>), nblk, 256, shm, st, Q, g->N, nchunk, phat, seedlab, mdev,
+                  rpb, part, g->status);
+      } else {
+        const size_t shm = sizeof(float) * kParts * (size_t)nchunk * 8 * LP;
+        if (shm > 48 * 1024)
+          cudaFuncSetAttribute(k_project_cw<T, LP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+        RW_LAUNCH((k_project_cw<T, LP>), nblk, 256, shm, st, Q, g->N, nchunk, phat, seedlab, mdev,
+                  rpb, part);
+      }
     } else {
       const size_t shm = sizeof(float) * (size_t)((nchunk + kBackChunks - 1) / kBackChunks * kBackChunks) * 8 * LP;
       RW_LAUNCH((k_backproject_panel<T, LP>), nblk, 256, shm, st, Q, g->N, nchunk, C, cscale, seedlab,
