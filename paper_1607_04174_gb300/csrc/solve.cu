@@ -652,69 +652,55 @@ __device__ void lu_diag_rot(float* A, int ms, int k0, int kb, float* buf, const 
   __syncwarp();
 }
 
-// ---------------------------------------------------------------------------------------
-// 32 x 32 blocks on 128 threads: thread t keeps eight entries of row (or column) t / 4, the
-// quarter t % 4, in registers, so a step is eight FMAs per thread.  Values of another quarter of
-// the same row come by a shuffle inside the row's four lanes; what every row needs (a pivot row
-// or column) goes through shared memory with one named barrier per step (double-buffered).
-// The step loop runs over the owning quarter (rolled) and the entry inside it (unrolled), so
-// every register index is a constant.
-// ---------------------------------------------------------------------------------------
-__device__ __forceinline__ void bar_sync_128() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+// LU without pivoting of the kb x kb diagonal block at (k0, k0) by one warp, branch-free steps:
+// lane r keeps row r in shifted registers; at step kk the pivot lane publishes its row (shifted
+// by one) and the pivot through shared memory, every lane stores one entry of that U row into
+// A, the lanes below write their multiplier, and every lane runs the shifted update (rows at or
+// above the pivot only produce values that are never stored).  uinv[k0 + c] = 1 / U_cc; a zero
+// pivot is replaced by 1e-30.  buf: 128 floats, 16-byte aligned.
+__device__ void lu_diag_warp(float* A, int ms, int k0, int kb, float* buf, float* uinv) {
+  const int lane = threadIdx.x & 31;
+  const bool live = lane < kb;
+  float* row = A + (size_t)(k0 + (live ? lane : 0)) * ms + k0;
+  float a[32];
+#pragma unroll
+  for (int c = 0; c < 32; ++c) a[c] = (live && c < kb) ? row[c] : (c == lane ? 1.f : 0.f);
+  for (int kk = 0; kk < kb; ++kk) {
+    float* b = buf + 64 * (kk & 1);
+    if (lane == kk) {
+#pragma unroll
+      for (int t4 = 0; t4 < 8; ++t4)
+        reinterpret_cast<float4*>(b)[t4] =
+            make_float4(a[4 * t4 + 1], a[4 * t4 + 2], a[4 * t4 + 3], t4 < 7 ? a[4 * t4 + 4] : 0.f);
+      b[32] = a[0];
+    }
+    __syncwarp();
+    float u = b[32];
+    float4 v[8];
+    load_bcast(v, b);
+    if (u == 0.f) u = 1e-30f;
+    const float ru = 1.f / u;
+    // U_kk,kk+1+lane from the published row; the pivot itself by lane 0
+    float* urow = A + (size_t)(k0 + kk) * ms + k0 + kk;
+    if (lane + kk + 1 < kb) urow[1 + lane] = b[lane];
+    if (lane == 0) { urow[0] = b[32]; uinv[k0 + kk] = ru; }
+    const float f = a[0] * ru;
+    if (live && lane > kk) row[kk] = f;  // multiplier L_lane,kk
+    shift_update_r(a, f, v);
+  }
+  __syncwarp();
+}
 
+// ---------------------------------------------------------------------------------------
+// Triangular solves of 32-row (32-column) panels on 128 threads: thread t keeps eight entries
+// of row (or column) t / 4, the quarter t % 4, in registers, so a step is eight FMAs per
+// thread; the value that every row needs comes by a shuffle inside the row's four lanes.  The
+// step loop runs over the owning quarter (rolled) and the entry inside it (unrolled), so every
+// register index is a constant.
+// ---------------------------------------------------------------------------------------
 __device__ __forceinline__ void unpack8(const float4& v0, const float4& v1, float (&p)[8]) {
   p[0] = v0.x; p[1] = v0.y; p[2] = v0.z; p[3] = v0.w;
   p[4] = v1.x; p[5] = v1.y; p[6] = v1.z; p[7] = v1.w;
-}
-
-// LU without pivoting of the kb x kb diagonal block at (k0, k0) by threads 0..127 (unit-lower
-// multipliers below the diagonal, U on and above); uinv[k0 + c] = 1 / U_cc.  P: 80 floats,
-// 16-byte aligned.  A pivot below 1e-3 dref (when dref is given) sets *unstable; a zero pivot is
-// replaced by 1e-30.
-__device__ void lu_diag_128(float* A, int ms, int k0, int kb, float* P, float* uinv,
-                            const float* dref, int* unstable) {
-  const int t = threadIdx.x, r = t >> 2, g = t & 3, src = (t & 31) & ~3;
-  const bool live = r < kb;
-  float* row = A + (size_t)(k0 + (live ? r : 0)) * ms + k0 + 8 * g;
-  float a[8];
-#pragma unroll
-  for (int q = 0; q < 8; ++q) a[q] = (live && 8 * g + q < kb) ? row[q] : 0.f;
-  for (int go = 0; go < 4; ++go) {
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      const int kk = 8 * go + j;
-      if (kk < kb) {
-        float* p = P + 40 * (kk & 1);
-        if (r == kk) {
-          reinterpret_cast<float4*>(p)[2 * g] = make_float4(a[0], a[1], a[2], a[3]);
-          reinterpret_cast<float4*>(p)[2 * g + 1] = make_float4(a[4], a[5], a[6], a[7]);
-        }
-        const float ark = __shfl_sync(0xffffffff, a[j], src | go);  // A_r,kk from its owner
-        bar_sync_128();
-        float pv[8];
-        unpack8(reinterpret_cast<const float4*>(p)[2 * g], reinterpret_cast<const float4*>(p)[2 * g + 1], pv);
-        float u = p[kk];
-        if (dref && t == 0 && !(fabsf(u) >= 1e-3f * dref[k0 + kk])) *unstable = 1;
-        if (u == 0.f) u = 1e-30f;
-        if (t == 4 * kk) uinv[k0 + kk] = 1.f / u;
-        if (r > kk) {
-          const float f = __fdividef(ark, u);
-#pragma unroll
-          for (int q = 0; q < 8; ++q) {
-            const int col = 8 * g + q;
-            if (col > kk) a[q] = fmaf(-f, pv[q], a[q]);
-            else if (col == kk) a[q] = f;
-          }
-        }
-      }
-    }
-  }
-  if (live) {
-#pragma unroll
-    for (int q = 0; q < 8; ++q)
-      if (8 * g + q < kb) row[q] = a[q];
-  }
-  bar_sync_128();
 }
 
 // Rows r0 .. r0 + nr of the 32 columns at c0 times U^{-1} (U the block at (c0, c0)): threads
@@ -1844,9 +1830,9 @@ __device__ void lu_body(cg::cluster_group& cl, int mmax, const float* __restrict
   __shared__ float lg[kMaxSmallM], uinv[kMaxSmallM];
   __shared__ __align__(16) float Ush[32 * 32], Lsh[32 * 32];
   __shared__ __align__(16) float buf[128];
-  __shared__ int dec, unstable, flag;
+  __shared__ int dec, unstable;
   for (int i = tid; i < mmax; i += blockDim.x) lg[i] = (float)(lam[i] + gamma);
-  if (tid == 0) { unstable = 0; flag = 0; }
+  if (tid == 0) unstable = 0;
   __syncthreads();
   lu_load_border(A, ms, 0, mmax, Kg, ldk, lg, dmax, 0);
   __syncthreads();
@@ -1869,9 +1855,9 @@ __device__ void lu_body(cg::cluster_group& cl, int mmax, const float* __restrict
     }
     if (synced && covered >= target) break;
     lu_solve_border(A, ms, T, mmax, Ush, Lsh, uinv);
-    if (threadIdx.x < 128)
-      lu_diag_128(A, ms, 32 * T, min(32, mmax - 32 * T), buf, uinv, nullptr, &flag);
-    else if (32 * (T + 1) < mmax)
+    if (threadIdx.x < 32)
+      lu_diag_warp(A, ms, 32 * T, min(32, mmax - 32 * T), buf, uinv);
+    else if (threadIdx.x >= 128 && 32 * (T + 1) < mmax)
       lu_load_border(A, ms, T + 1, mmax, Kg, ldk, lg, dmax, 4);
     __syncthreads();
     ++T;
