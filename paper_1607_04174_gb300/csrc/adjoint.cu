@@ -16,10 +16,6 @@
 // (s A s) x = s G.
 #include "rw_internal.cuh"
 
-rw_status rw_solve_priors_internal(const rw_graph* g, const int32_t* seed_idx,
-                                   const int32_t* seed_lab, int S, int L, int prior_mode,
-                                   const float* priors, int lp, cudaStream_t st, float** phat_out,
-                                   int** seedlab_out, double** fit64_out);
 rw_status rw_pcg_run(const rw_graph* g, const float* phat, const float* bexp, const int* seedlab,
                      int L, int lp, double gamma, const float* xhat0, int iters, double tol,
                      float* U, uint8_t* labels, int unscale_out, int* iters_done_dev,

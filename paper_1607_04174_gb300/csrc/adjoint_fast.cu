@@ -27,10 +27,6 @@
 #include <algorithm>
 #include <vector>
 
-rw_status rw_solve_priors_internal(const rw_graph* g, const int32_t* seed_idx,
-                                   const int32_t* seed_lab, int S, int L, int prior_mode,
-                                   const float* priors, int lp, cudaStream_t st, float** phat_out,
-                                   int** seedlab_out, double** fit64_out);
 
 namespace {
 

@@ -313,10 +313,6 @@ rw_status rw_pcg_from(const rw_graph* g, const float* phat, const int* seedlab, 
                     nullptr, nullptr, st);
 }
 
-rw_status rw_solve_priors_internal(const rw_graph* g, const int32_t* seed_idx,
-                                   const int32_t* seed_lab, int S, int L, int prior_mode,
-                                   const float* priors, int lp, cudaStream_t st, float** phat_out,
-                                   int** seedlab_out, double** fit64_out);
 
 extern "C" rw_status rw_solve_pcg(const rw_graph* g, const int32_t* seed_idx_dev,
                                   const int32_t* seed_lab_dev, int32_t S, int32_t n_labels,

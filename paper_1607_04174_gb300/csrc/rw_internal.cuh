@@ -98,6 +98,7 @@ struct SolveWorkspace {
   DevBuf seedlab;   // int [N]: -1 unseeded, else label
   DevBuf seedpart;  // seed-side sums: fit (FP64) and per-block label sums
   bool seeds_clean = false;  // seedlab is all -1 (the last solve's final kernel cleared it)
+  int seed_nsb = 0;          // scatter blocks of the last seed scatter (the priors fit reads them)
   DevBuf small;     // small per-solve arrays (stats, Q_s, X, products, Z, C, ...)
   DevBuf xhat[2];   // refinement iterates, N x lpad FP32
   DevBuf phat;      // hat-space priors, N x lpad FP32
@@ -189,6 +190,18 @@ size_t rw_sym_eig_work_bytes(int n);
 rw_status rw_copy_cols(const float* src, int64_t lds, float* dst, int64_t ldd, int64_t N,
                        const int* cols, int ncols, cudaStream_t st);
 rw_status rw_f64_to_f32(const double* a, float* b, int64_t n, cudaStream_t st);
+
+// Seed bookkeeping shared by the fast solve, the PCG solve and the gradients: resets the label
+// array when needed, scatters the seeds (per-block label statistics) and, unless deferred,
+// launches the priors kernel; launch_priors launches it later (early = 1: other kernels were
+// launched in between, see k_priors).
+rw_status rw_solve_priors_internal(const rw_graph* g, const int32_t* seed_idx,
+                                   const int32_t* seed_lab, int S, int L, int prior_mode,
+                                   const float* priors, int lp, cudaStream_t st, float** phat_out,
+                                   int** seedlab_out, double** fit64_out,
+                                   bool defer_priors = false);
+rw_status launch_priors(const rw_graph* g, int L, int prior_mode, const float* priors, int lp,
+                        int early, cudaStream_t st);
 
 // update.cu: edge-sum Rayleigh quotients of every basis column under g -> b->lam (synchronizes)
 rw_status rw_basis_rayleigh(const rw_graph* g, rw_basis* b, cudaStream_t st);

@@ -177,11 +177,11 @@ __device__ void seed_fit(const float* __restrict__ bpart, int nsb, int L, int pr
   float n = 0.f, mean = 0.f, m2 = 0.f;
   for (int b = 0; b < nsb; ++b) {
     const float* o = bpart + ((size_t)b * L + k) * 3;
-    const float nb = o[0];
+    const float nb = __ldcg(o);
     if (nb > 0.f) {
-      const float nt = n + nb, delta = o[1] - mean;
+      const float nt = n + nb, delta = __ldcg(o + 1) - mean;
       mean += delta * (nb / nt);
-      m2 += o[2] + delta * delta * (n * nb / nt);
+      m2 += __ldcg(o + 2) + delta * delta * (n * nb / nt);
       n = nt;
     }
   }
@@ -203,8 +203,11 @@ template <int LP>
 __global__ void __launch_bounds__(256)
 k_priors(const float* __restrict__ J, const float* __restrict__ sq, int64_t N, int L,
          int prior_mode, const float* __restrict__ bpart, int nsb, double* __restrict__ fit64,
-         const float* __restrict__ Pin, float* __restrict__ phat, int* status) {
-  rw_grid_wait();
+         const float* __restrict__ Pin, float* __restrict__ phat, int* status, int early) {
+  // early: launched behind kernels that do not touch its inputs (they come from further back
+  // and are complete once its predecessor has started), so it starts at once and waits for
+  // its predecessor only before it exits; the kernels after it then see both
+  if (!early) rw_grid_wait();
   rw_grid_trigger();
   __shared__ float fit[48];
   if (prior_mode == 0)
@@ -279,6 +282,7 @@ k_priors(const float* __restrict__ J, const float* __restrict__ sq, int64_t N, i
                             rv[u] * p[4 * k4 + 3]);
     }
   }
+  if (early) rw_grid_wait();
 }
 
 // One warp per seed: Q_s row, X = B-hat Q_n row, U-hat_s row, r0 = L-hat_s U-hat_s + g U-hat_s
@@ -2677,10 +2681,6 @@ __global__ void k_f32_to_bf16(const float* __restrict__ a, int64_t N, int m, int
 
 }  // namespace
 
-rw_status rw_solve_priors_internal(const rw_graph* g, const int32_t* seed_idx,
-                                   const int32_t* seed_lab, int S, int L, int prior_mode,
-                                   const float* priors, int lp, cudaStream_t st, float** phat_out,
-                                   int** seedlab_out, double** fit64_out);
 
 // launches k_seed_gram with the seed rows split over a cluster of up to 8 CTAs along z
 // The cluster-fused adaptive choice + LU (k_adapt_lu) when both CTAs' shared memory fits;
@@ -2759,7 +2759,7 @@ static rw_status seed_gram(const float* A, int lda, const float* B, int ldb, int
 rw_status rw_solve_priors_internal(const rw_graph* g, const int32_t* seed_idx,
                                    const int32_t* seed_lab, int S, int L, int prior_mode,
                                    const float* priors, int lp, cudaStream_t st, float** phat_out,
-                                   int** seedlab_out, double** fit64_out) {
+                                   int** seedlab_out, double** fit64_out, bool defer_priors) {
   rw_graph* gm = const_cast<rw_graph*>(g);
   SolveWorkspace& ws = gm->ws;
   if (S > kMaxSeeds) return RW_ERR_INVALID_ARG;
@@ -2778,22 +2778,35 @@ rw_status rw_solve_priors_internal(const rw_graph* g, const int32_t* seed_idx,
   if (!ws.seeds_clean)
     RW_LAUNCH(k_seed_reset, rw_blocks(g->N, 256), 256, 0, st, seedlab, g->N, nullptr, 0);
   ws.seeds_clean = false;
-  const int sms = g_rw_num_sms > 0 ? g_rw_num_sms : 148;
-  const int pblk = (int)std::min<int64_t>(rw_blocks((g->N + 3) / 4, 256), 8 * sms);
+  ws.seed_nsb = nsb;
   RW_LAUNCH(k_seed_scatter, nsb, 256, 0, st, seed_idx, seed_lab, S, L, g->N,
             g->J ? g->J : nullptr, seedlab, bpart, g->status);
-  if (lp == 4)
-    RW_LAUNCH(k_priors<4>, pblk, 256, 0, st, g->J, g->sq, g->N, L, prior_mode,
-              bpart, nsb, fit64, priors, ws.phat.as<float>(), g->status);
-  else if (lp == 8)
-    RW_LAUNCH(k_priors<8>, pblk, 256, 0, st, g->J, g->sq, g->N, L, prior_mode,
-              bpart, nsb, fit64, priors, ws.phat.as<float>(), g->status);
-  else
-    RW_LAUNCH(k_priors<16>, pblk, 256, 0, st, g->J, g->sq, g->N, L, prior_mode,
-              bpart, nsb, fit64, priors, ws.phat.as<float>(), g->status);
+  if (!defer_priors) RW_TRY(launch_priors(g, L, prior_mode, priors, lp, 0, st));
   *phat_out = ws.phat.as<float>();
   *seedlab_out = seedlab;
   if (fit64_out) *fit64_out = fit64;
+  return RW_OK;
+}
+
+// The priors kernel for the seeds scattered by the last rw_solve_priors_internal call on g;
+// early = 1 when other kernels were launched in between (see k_priors).
+rw_status launch_priors(const rw_graph* g, int L, int prior_mode, const float* priors, int lp,
+                        int early, cudaStream_t st) {
+  SolveWorkspace& ws = const_cast<rw_graph*>(g)->ws;
+  const int nsb = ws.seed_nsb;
+  float* bpart = reinterpret_cast<float*>(ws.seedpart.as<char>() + 4096);
+  double* fit64 = ws.seedpart.as<double>();
+  const int sms = g_rw_num_sms > 0 ? g_rw_num_sms : 148;
+  const int pblk = (int)std::min<int64_t>(rw_blocks((g->N + 3) / 4, 256), 8 * sms);
+  if (lp == 4)
+    RW_LAUNCH(k_priors<4>, pblk, 256, 0, st, g->J, g->sq, g->N, L, prior_mode,
+              bpart, nsb, fit64, priors, ws.phat.as<float>(), g->status, early);
+  else if (lp == 8)
+    RW_LAUNCH(k_priors<8>, pblk, 256, 0, st, g->J, g->sq, g->N, L, prior_mode,
+              bpart, nsb, fit64, priors, ws.phat.as<float>(), g->status, early);
+  else
+    RW_LAUNCH(k_priors<16>, pblk, 256, 0, st, g->J, g->sq, g->N, L, prior_mode,
+              bpart, nsb, fit64, priors, ws.phat.as<float>(), g->status, early);
   return RW_OK;
 }
 
@@ -2871,8 +2884,10 @@ extern "C" rw_status rw_solve(const rw_graph* g, const rw_basis* b, const int32_
   float* phat = nullptr;
   int* seedlab = nullptr;
   double* fit64 = nullptr;
+  // seeds scattered now; the priors kernel runs behind the seed-side products (it only needs
+  // the scatter) and overlaps them
   RW_TRY(rw_solve_priors_internal(g, seed_idx_dev, seed_lab_dev, S, L, opts->prior_mode,
-                                  priors_dev, lp, st, &phat, &seedlab, &fit64));
+                                  priors_dev, lp, st, &phat, &seedlab, &fit64, true));
 
   RW_TRY(mark(1));
   const int wcat = 2 * mp + 2 * lp;
@@ -2889,6 +2904,7 @@ extern "C" rw_status rw_solve(const rw_graph* g, const rw_basis* b, const int32_
       g->sq, g->normalized, g->kind, g->ndim, g->dims[0], g->dims[1], g->dims[2], g->rowptr,
       g->col, g->ccsr, (float)gamma, Bcat, wcat);
   RW_TRY(seed_gram(Qs, wcat, Bcat, wcat, S, m_max, wcat, Gcat, wcat, st));
+  RW_TRY(launch_priors(g, L, opts->prior_mode, priors_dev, lp, phases ? 0 : 1, st));
   double* fu = reinterpret_cast<double*>(P(lay.fu));
   double* fsel = fu + (size_t)(ncand + 1) * RW_MAX_LABELS;
   RW_TRY(mark(2));
