@@ -287,9 +287,10 @@ def equal_accuracy(rw, g, b, dsets, conv, tmp, labels, flush, stream, kw, pcg_ms
             "pcg_label_maps_per_s": 1000.0 / pcg_ms, "speedup_vs_pcg": pcg_ms / ms}
 
 
-def c3_block(rw, torch, dev, flush, stream, steps=100):
+def c3_block(rw, torch, dev, flush, stream, steps=100, quick=False):
     """The 128^3 volume (6-connected, 2 labels, 500 seeds per label, m = 100): precompute,
-    online solves (adaptive m, 3 refinement steps), and the equal-accuracy comparison."""
+    online solves (adaptive m, 3 refinement steps), and the equal-accuracy comparison (skipped
+    when quick: timing and phases only, for profiling runs)."""
     J, dims, truth = synth.ellipsoid_volume(128, seed=synth.BASE_SEED + 2)
     N = int(np.prod(dims))
     g = rw.rw_build_graph(torch.from_numpy(J.astype(np.float32)).to(dev), dims, BETA)
@@ -310,6 +311,12 @@ def c3_block(rw, torch, dev, flush, stream, steps=100):
     infos = [rw.rw_solve(g, b, dp[k % 20][0], dp[k % 20][1], 2, prob, lab, record_phases=True,
                          **kw)[1] for k in range(40)]
     phases = {p: float(np.mean([i["phase_ms"][p] for i in infos])) for p in rw.RW_PHASES}
+    if quick:
+        rw.rw_basis_free(b)
+        rw.rw_graph_free(g)
+        return {"workload": "rwis-128x128x128-2label-ellipsoid", "label_maps_per_s": 1000.0 / ms,
+                "ms_per_step": ms, "steps": steps, "phase_ms": phases,
+                "partial": "profiling run (--c3-only)"}
     si0, sl0 = dp[0]
     conv = torch.empty(N, 2, device=dev)
     tmp = torch.empty(N, 2, device=dev)
@@ -369,6 +376,13 @@ def gpu_arm(args):
         with open(pk) as f:
             peaks = json.load(f)
 
+    if args.c3_only:  # profiling runs of the 128^3 workload
+        flush = torch.empty(L2_FLUSH_BYTES // 4, device=dev)
+        out = c3_block(rw, torch, dev, flush, torch.cuda.current_stream(), steps=args.steps,
+                       quick=True)
+        if rank == 0:
+            print(json.dumps(out))
+        return 0
     J, dims, truth = synth.voronoi_image(SIZE, SIZE, seed=synth.BASE_SEED + 1)
     N = SIZE * SIZE
     J32 = torch.from_numpy(J.astype(np.float32)).to(dev)
@@ -551,6 +565,8 @@ def main():
     ap.add_argument("--no-competitor", action="store_true",
                     help="skip the e2e, PCG and CPU legs (profiling runs)")
     ap.add_argument("--no-c3", action="store_true", help="skip the 128^3 block")
+    ap.add_argument("--c3-only", action="store_true",
+                    help="only time the 128^3 workload (profiling runs)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

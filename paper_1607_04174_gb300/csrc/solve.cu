@@ -75,6 +75,11 @@ __device__ __forceinline__ void cp_async16(float* dst, const float* src) {
                :: "r"((unsigned)__cvta_generic_to_shared(dst)), "l"(src) : "memory");
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+// 16 bytes, or zeros when !valid (source size 0; src must still be a valid address)
+__device__ __forceinline__ void cp_async16_zfill(void* dst, const void* src, bool valid) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;"
+               :: "r"((unsigned)__cvta_generic_to_shared(dst)), "l"(src), "r"(valid ? 16 : 0) : "memory");
+}
 
 // mbarrier + bulk asynchronous copy (global -> shared, completion counted in bytes on the
 // barrier).  Waits are bounded: a wait that gives up sets RW_DEV_TIMEOUT.
@@ -350,11 +355,30 @@ __global__ void k_seed_gather(const int32_t* __restrict__ idx, const int32_t* __
       nc[2 * a] = lo ? cw[a * N + i - st[a]] : 0.f;
       nc[2 * a + 1] = hi ? cw[a * N + i] : 0.f;
     }
+    // the neighbours' rows of Q and d^{1/2} are requested together with their labels (one
+    // round trip); a seeded neighbour's row is then dropped
+    float qn[6][7], sn[6];
 #pragma unroll
-    for (int u = 0; u < 6; ++u) nl[u] = nj[u] >= 0 ? seedlab[nj[u]] : -2;
+    for (int u = 0; u < 6; ++u) {
+      nl[u] = nj[u] >= 0 ? seedlab[nj[u]] : -2;
+      sn[u] = nj[u] >= 0 ? sq[nj[u]] : 0.f;
+      const float* qj = Q + (nj[u] >= 0 ? nj[u] : 0) * ldq;
 #pragma unroll
-    for (int u = 0; u < 6; ++u)
-      if (nj[u] >= 0) visit(nj[u], nc[u], nl[u]);
+      for (int q = 0; q < 7; ++q) {
+        const int cc = lane + 32 * q;
+        qn[u][q] = (nj[u] >= 0 && cc < mp) ? qj[cc] : 0.f;
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 6; ++u) {
+      if (nj[u] < 0) continue;
+      if (nl[u] < 0) {
+#pragma unroll
+        for (int q = 0; q < 7; ++q) acc[q] = fmaf(-nc[u], qn[u][q], acc[q]);
+      } else if (lane == nl[u]) {
+        r0 -= nc[u] * sn[u];
+      }
+    }
   } else {
     for (int p = rowptr[i]; p < rowptr[i + 1]; ++p) visit(colv[p], ccsr[p], seedlab[colv[p]]);
   }
@@ -1022,18 +1046,17 @@ k_seed_gram(const float* __restrict__ A, int lda, const float* __restrict__ B, i
   const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
   float acc[4][4] = {};
   for (int k0 = r0; k0 < r1; k0 += kSgRows) {
-    // the whole stage (kSgRows rows of the two 64-column tiles) in flight before one barrier
+    // the whole stage (kSgRows rows of the two 64-column tiles) requested at once (cp.async,
+    // zero-filled outside the rows / columns), one round trip before one barrier
     for (int e = threadIdx.x; e < kSgRows * 16; e += 256) {
       const int kk = e / 16, c4 = e % 16;
       const int r = k0 + kk;
       const bool rin = r < r1;
-      As[kk * 17 + c4] = (rin && i0 + 4 * c4 < p)
-          ? __ldg(reinterpret_cast<const float4*>(A + (int64_t)r * lda + i0) + c4)
-          : make_float4(0.f, 0.f, 0.f, 0.f);
-      Bs[kk * 17 + c4] = (rin && j0 + 4 * c4 < q)
-          ? __ldg(reinterpret_cast<const float4*>(B + (int64_t)r * ldb + j0) + c4)
-          : make_float4(0.f, 0.f, 0.f, 0.f);
+      const bool ain = rin && i0 + 4 * c4 < p, bin = rin && j0 + 4 * c4 < q;
+      cp_async16_zfill(As + kk * 17 + c4, ain ? A + (int64_t)r * lda + i0 + 4 * c4 : A, ain);
+      cp_async16_zfill(Bs + kk * 17 + c4, bin ? B + (int64_t)r * ldb + j0 + 4 * c4 : B, bin);
     }
+    cp_async_wait_all();
     __syncthreads();
     const int kn = min(kSgRows, r1 - k0);
 #pragma unroll 4
@@ -1051,25 +1074,29 @@ k_seed_gram(const float* __restrict__ A, int lda, const float* __restrict__ B, i
   for (int u = 0; u < 4; ++u)
     part[(ty * 4 + u) * 16 + tx] = make_float4(acc[u][0], acc[u][1], acc[u][2], acc[u][3]);
   cluster.sync();
-  if (rank == 0) {
+  // every rank sums its share of the tile's float4 entries over the ranks, in rank order
+  const int per = (kSgT * kSgT / 4 + nz - 1) / nz;
+  const int e0 = rank * per, e1 = min(kSgT * kSgT / 4, e0 + per);
+  for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+    float4 v[kSgMaxCluster];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      float4 sum = part[(ty * 4 + u) * 16 + tx];
-      for (int r = 1; r < nz; ++r) {
-        const float4 o = cluster.map_shared_rank(part, r)[(ty * 4 + u) * 16 + tx];
-        sum.x += o.x; sum.y += o.y; sum.z += o.z; sum.w += o.w;
+    for (int r = 0; r < kSgMaxCluster; ++r)
+      if (r < nz) v[r] = cluster.map_shared_rank(part, r)[e];
+    float4 sum = v[0];
+#pragma unroll
+    for (int r = 1; r < kSgMaxCluster; ++r)
+      if (r < nz) { sum.x += v[r].x; sum.y += v[r].y; sum.z += v[r].z; sum.w += v[r].w; }
+    const int row = e / 16, c4 = e % 16;   // part[(ty * 4 + u) * 16 + tx]: row ty * 4 + u
+    const int i = i0 + row;
+    const float vals[4] = {sum.x, sum.y, sum.z, sum.w};
+    if (i < p)
+#pragma unroll
+      for (int w = 0; w < 4; ++w) {
+        const int j = j0 + c4 * 4 + w;
+        if (j < q) Gout[(int64_t)i * ldg + j] = vals[w];
       }
-      const int i = i0 + ty * 4 + u;
-      const float vals[4] = {sum.x, sum.y, sum.z, sum.w};
-      if (i < p)
-#pragma unroll
-        for (int v = 0; v < 4; ++v) {
-          const int j = j0 + tx * 4 + v;
-          if (j < q) Gout[(int64_t)i * ldg + j] = vals[v];
-        }
-    }
   }
-  cluster.sync();  // the peers' partial tiles stay alive until rank 0 has read them
+  cluster.sync();  // the peers' partial tiles stay alive until every rank has read them
 }
 
 // ---------------------------------------------------------------------------------------
