@@ -188,10 +188,10 @@ SMS, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0   # GB300: FP32 lanes per SM, max
 def phase_work(phase, N, m, lp, S, L, steps):
     """(bound, algorithmic units per launch, unit) of each phase of one solve: HBM bytes the
     phase must move at minimum, or FP32 flops of its dense factorizations."""
-    if phase == "seeds":     # seed labels (N i32 written), intensities read, hat priors written
-        return "hbm", N * (4 + 4 + 4 * lp), "B"
+    if phase == "seeds":     # seed scatter: index, label, intensity read, label written
+        return "hbm", S * (4 + 4 + 4 + 4), "B"
     if phase == "gather":    # seed rows of Q and neighbour rows (FP32), Gram of [X Q_s r U]
-        return "alu", 2.0 * S * m * (2 * m + 2 * lp), "flop"
+        return "alu", 2.0 * S * m * (2 * m + 2 * lp), "flop"  # (+ the priors kernel beside it)
     if phase == "adapt":     # Cholesky of G_m + solves for the labels, LU of the m x m system
         return "alu", m ** 3 / 3.0 + 2.0 * L * m * m + 2.0 * m ** 3 / 3.0, "flop"
     if phase == "small":     # the two triangular solves per label
@@ -205,8 +205,13 @@ def phase_work(phase, N, m, lp, S, L, steps):
     raise KeyError(phase)
 
 
-PHASE_KERNELS = {"seeds": "k_seed_scatter+k_priors",
-                 "gather": "k_seed_gather+k_seed_gram", "adapt": "k_adapt_lu",
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from an ncu --set full
+# capture of the kernel at 512x512, 4 labels; the dense fused kernel reads only the m x m
+# matrices it factors
+NCU_DRAM_BYTES = {"k_adapt_lu": 447232}
+
+PHASE_KERNELS = {"seeds": "k_seed_scatter",
+                 "gather": "k_seed_gather+k_seed_gram+k_priors", "adapt": "k_adapt_lu",
                  "project": "k_project_cw+k_reduce_partials", "small": "k_small_rhs",
                  "back": "k_backproject_panel", "refine": "k_jacobi_grid x3"}
 
@@ -229,7 +234,7 @@ def rooflines(phases, N, m, lp, S, L, steps, hbm, sm_mhz):
     dom = max(phases, key=lambda p: phases[p])
     top = dict(table[dom])
     top["phase"] = dom
-    top["traffic"] = None
+    top["traffic"] = NCU_DRAM_BYTES.get(top["kernel"])
     return top, table
 
 
