@@ -24,6 +24,8 @@
 #include <cooperative_groups.h>
 
 #include <algorithm>
+#include <mutex>
+#include <unordered_map>
 #include <cstring>
 
 namespace cg = cooperative_groups;
@@ -58,6 +60,23 @@ Layout make_layout(int S, int mp, int mq, int lp, int L, int ncand, int nblk_par
   o.part = take(sizeof(float) * (size_t)nblk_part * mq * lp);
   o.total = off;
   return o;
+}
+
+// cudaFuncSetAttribute(MaxDynamicSharedMemorySize) only when a kernel needs more than it was
+// last given (host side; the per-solve call path stays free of attribute calls once warm)
+template <typename F>
+static cudaError_t ensure_smem(F* func, size_t bytes) {
+  static std::mutex mu;
+  static std::unordered_map<const void*, size_t> done[64];  // per device
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64)
+    return cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  std::lock_guard<std::mutex> lock(mu);
+  size_t& have = done[dev][reinterpret_cast<const void*>(func)];
+  if (bytes <= have) return cudaSuccess;
+  const cudaError_t e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess) have = bytes;
+  return e;
 }
 
 __device__ __forceinline__ float warp_sum(float v) {
@@ -2644,13 +2663,13 @@ rw_status launch_proj_back(bool back, const T* Q, int ldq, const float* phat,
       const int64_t rpb = (g->N + nblk - 1) / nblk;
       if constexpr (LP <= 8) {
         const size_t shm = sizeof(uint4) * kPtStages * kPtRows + sizeof(float) * 8 * (size_t)nchunk * 8 * LP;
-        cudaFuncSetAttribute(k_project_tma<T, LP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+        RW_CHECK_CUDA(ensure_smem(k_project_tma<T, LP>, shm));
         RW_LAUNCH((k_project_tma<T, LP>), nblk, 256, shm, st, Q, g->N, nchunk, phat, seedlab, mdev,
                   rpb, part, g->status);
       } else {
         const size_t shm = sizeof(float) * kParts * (size_t)nchunk * 8 * LP;
         if (shm > 48 * 1024)
-          cudaFuncSetAttribute(k_project_cw<T, LP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+          RW_CHECK_CUDA(ensure_smem(k_project_cw<T, LP>, shm));
         RW_LAUNCH((k_project_cw<T, LP>), nblk, 256, shm, st, Q, g->N, nchunk, phat, seedlab, mdev,
                   rpb, part);
       }
@@ -2733,7 +2752,7 @@ static rw_status launch_adapt_lu(size_t shm, cudaStream_t st, const float* G, co
                                  int m_max, int m_step, double rho, double fmax, int adaptive,
                                  const float* K, const double* lam, double gamma, float* F,
                                  int ldf, float* luinv, int* mdev, double* fsel) {
-  RW_CHECK_CUDA(cudaFuncSetAttribute(k_adapt_lu<LP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+  RW_CHECK_CUDA(ensure_smem(k_adapt_lu<LP>, shm));
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(2, 1, 1);
   cfg.blockDim = dim3(256, 1, 1);
@@ -2760,7 +2779,7 @@ static rw_status seed_gram(const float* A, int lda, const float* B, int ldb, int
   // enough CTAs along z that each holds at most one stage of rows (up to the cluster limit)
   const int nz = std::max(1, std::min(kSgMaxCluster, (S + kSgRows - 1) / kSgRows));
   const size_t shm = sizeof(float4) * 2 * kSgRows * 17;
-  RW_CHECK_CUDA(cudaFuncSetAttribute(k_seed_gram, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+  RW_CHECK_CUDA(ensure_smem(k_seed_gram, shm));
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((p + kSgT - 1) / kSgT, (q + kSgT - 1) / kSgT, nz);
   cfg.blockDim = dim3(256, 1, 1);
@@ -2958,15 +2977,15 @@ extern "C" rw_status rw_solve(const rw_graph* g, const rw_basis* b, const int32_
   } else if (adaptive) {
     const size_t shm = sizeof(float) * ((size_t)m_max * (m_max | 1) + 3 * (size_t)L * m_max);
     if (lp == 4) {
-      cudaFuncSetAttribute(k_adapt<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+      RW_CHECK_CUDA(ensure_smem(k_adapt<4>, shm));
       RW_LAUNCH((k_adapt<4>), 1, 256, shm, st, G, wcat, bv, wcat, Qs, wcat, Us, wcat, S, L, m_max, m_step,
                                       rho, fmax, mdev, fsel);
     } else if (lp == 8) {
-      cudaFuncSetAttribute(k_adapt<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+      RW_CHECK_CUDA(ensure_smem(k_adapt<8>, shm));
       RW_LAUNCH((k_adapt<8>), 1, 256, shm, st, G, wcat, bv, wcat, Qs, wcat, Us, wcat, S, L, m_max, m_step,
                                       rho, fmax, mdev, fsel);
     } else {
-      cudaFuncSetAttribute(k_adapt<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+      RW_CHECK_CUDA(ensure_smem(k_adapt<16>, shm));
       RW_LAUNCH((k_adapt<16>), 1, 256, shm, st, G, wcat, bv, wcat, Qs, wcat, Us, wcat, S, L, m_max, m_step,
                                        rho, fmax, mdev, fsel);
     }
@@ -3011,28 +3030,28 @@ extern "C" rw_status rw_solve(const rw_graph* g, const rw_basis* b, const int32_
       shm = std::max(shm, sizeof(float) * ((size_t)m_max * lu_stride(m_max) + (size_t)(m_max + 32) * lp));
     if (fused) {
       if (lp == 4) {
-        cudaFuncSetAttribute(k_small_rhs<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+        RW_CHECK_CUDA(ensure_smem(k_small_rhs<4>, shm));
         RW_LAUNCH((k_small_rhs<4>), 1, 256, shm, st, K, wcat, h, wcat, Z, lgam, (float)gamma, L, lp, mq,
                   mdev, Fac, mp, luinv, C, g->status);
       } else if (lp == 8) {
-        cudaFuncSetAttribute(k_small_rhs<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+        RW_CHECK_CUDA(ensure_smem(k_small_rhs<8>, shm));
         RW_LAUNCH((k_small_rhs<8>), 1, 256, shm, st, K, wcat, h, wcat, Z, lgam, (float)gamma, L, lp, mq,
                   mdev, Fac, mp, luinv, C, g->status);
       } else {
-        cudaFuncSetAttribute(k_small_rhs<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+        RW_CHECK_CUDA(ensure_smem(k_small_rhs<16>, shm));
         RW_LAUNCH((k_small_rhs<16>), 1, 256, shm, st, K, wcat, h, wcat, Z, lgam, (float)gamma, L, lp, mq,
                   mdev, Fac, mp, luinv, C, g->status);
       }
     } else if (lp == 4) {
-      cudaFuncSetAttribute(k_small_solve<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+      RW_CHECK_CUDA(ensure_smem(k_small_solve<4>, shm));
       RW_LAUNCH((k_small_solve<4>), 1, 256, shm, st, K, wcat, h, wcat, Z, lgam, (float)gamma, L, lp, mq, mdev, C,
                                             g->status);
     } else if (lp == 8) {
-      cudaFuncSetAttribute(k_small_solve<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+      RW_CHECK_CUDA(ensure_smem(k_small_solve<8>, shm));
       RW_LAUNCH((k_small_solve<8>), 1, 256, shm, st, K, wcat, h, wcat, Z, lgam, (float)gamma, L, lp, mq, mdev, C,
                                             g->status);
     } else {
-      cudaFuncSetAttribute(k_small_solve<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+      RW_CHECK_CUDA(ensure_smem(k_small_solve<16>, shm));
       RW_LAUNCH((k_small_solve<16>), 1, 256, shm, st, K, wcat, h, wcat, Z, lgam, (float)gamma, L, lp, mq,
                                              mdev, C, g->status);
     }
