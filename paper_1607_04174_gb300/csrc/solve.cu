@@ -2376,8 +2376,99 @@ k_project_tma(const T* __restrict__ Qp, int64_t N, int nchunk_max, const float* 
 
 constexpr int kBackChunks = 8;  // 16-byte chunks per row in flight in the back-projection
 
+// VPI voxels per loop iteration, kBackChunks / VPI chunks of each in flight (all of an
+// iteration's loads issued before its arithmetic): VPI > 1 when few chunks are used, so that a
+// thread still keeps kBackChunks 16-byte loads in flight
+template <typename T, int LP, int VPI>
+__device__ __forceinline__ void backproject_rows(const T* __restrict__ Qp, int64_t N, int nch,
+                                                 const float* Cs, const int* __restrict__ seedlab,
+                                                 const float* __restrict__ sq,
+                                                 const float* __restrict__ s, int L,
+                                                 float* __restrict__ xhat, float* __restrict__ U,
+                                                 uint8_t* __restrict__ labels, int* clear_seedlab) {
+  constexpr int CPI = kBackChunks / VPI;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < N; i0 += VPI * stride) {
+    int sl[VPI];
+    float acc[VPI][LP];
+#pragma unroll
+    for (int w = 0; w < VPI; ++w) {
+      const int64_t i = i0 + w * stride;
+      sl[w] = i < N ? __ldg(seedlab + i) : 0;
+#pragma unroll
+      for (int k = 0; k < LP; ++k) acc[w][k] = 0.f;
+    }
+    for (int c = 0; c < nch; c += CPI) {
+      uint4 raw[VPI][CPI];
+#pragma unroll
+      for (int w = 0; w < VPI; ++w) {
+        const int64_t i = i0 + w * stride;
+#pragma unroll
+        for (int u = 0; u < CPI; ++u)
+          raw[w][u] = (i < N && c + u < nch)
+              ? __ldg(reinterpret_cast<const uint4*>(Qp + ((int64_t)(c + u) * N + i) * 8))
+              : make_uint4(0, 0, 0, 0);
+      }
+#pragma unroll
+      for (int u = 0; u < CPI; ++u) {
+        if (c + u < nch) {  // uniform over the block
+#pragma unroll
+          for (int w = 0; w < VPI; ++w) {
+            float q[8];
+            Vec16<T>::unpack(raw[w][u], q);
+#pragma unroll
+            for (int v = 0; v < 8; ++v) {
+              const float4* cr = reinterpret_cast<const float4*>(Cs + ((c + u) * 8 + v) * LP);
+#pragma unroll
+              for (int k4 = 0; k4 < LP / 4; ++k4) {
+                const float4 cv = cr[k4];
+                acc[w][4 * k4 + 0] = fmaf(q[v], cv.x, acc[w][4 * k4 + 0]);
+                acc[w][4 * k4 + 1] = fmaf(q[v], cv.y, acc[w][4 * k4 + 1]);
+                acc[w][4 * k4 + 2] = fmaf(q[v], cv.z, acc[w][4 * k4 + 2]);
+                acc[w][4 * k4 + 3] = fmaf(q[v], cv.w, acc[w][4 * k4 + 3]);
+              }
+            }
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int w = 0; w < VPI; ++w) {
+      const int64_t i = i0 + w * stride;
+      if (i >= N) break;
+      if (xhat) {
+        float4* xo = reinterpret_cast<float4*>(xhat + i * LP);
+#pragma unroll
+        for (int k4 = 0; k4 < LP / 4; ++k4) {
+          float o[4];
+#pragma unroll
+          for (int t = 0; t < 4; ++t) {
+            const int k = 4 * k4 + t;
+            o[t] = (k >= L) ? 0.f : ((sl[w] >= 0) ? (k == sl[w] ? sq[i] : 0.f) : acc[w][k]);
+          }
+          xo[k4] = make_float4(o[0], o[1], o[2], o[3]);
+        }
+      } else {
+        const float si = s[i];
+        int best = 0;
+        float bv = -INFINITY;
+#pragma unroll
+        for (int k = 0; k < LP; ++k) {
+          if (k < L) {
+            const float u = (sl[w] >= 0) ? (k == sl[w] ? 1.f : 0.f) : acc[w][k] * si;
+            U[i * L + k] = u;
+            if (u > bv) { bv = u; best = k; }
+          }
+        }
+        if (labels) labels[i] = (uint8_t)best;
+        if (clear_seedlab && sl[w] >= 0) clear_seedlab[i] = -1;
+      }
+    }
+  }
+}
+
 template <typename T, int LP>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 3)
 k_backproject_panel(const T* __restrict__ Qp, int64_t N, int nchunk_max,
                     const float* __restrict__ Cg, float cscale, const int* __restrict__ seedlab,
                     const float* __restrict__ sq, const float* __restrict__ s, int L,
@@ -2392,72 +2483,17 @@ k_backproject_panel(const T* __restrict__ Qp, int64_t N, int nchunk_max,
   for (int e = threadIdx.x; e < ncs * 8 * LP; e += blockDim.x)
     Cs[e] = e < nchunk_max * 8 * LP ? Cg[e] * cscale : 0.f;
   __syncthreads();
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    // the seed flag and the first chunks are loaded together (one round trip); seed rows
-    // discard the products
-    const int sl = __ldg(seedlab + i);
-    float acc[LP];
-#pragma unroll
-    for (int k = 0; k < LP; ++k) acc[k] = 0.f;
-    for (int c = 0; c < nch; c += kBackChunks) {  // kBackChunks chunks in flight
-      uint4 raw[kBackChunks];
-#pragma unroll
-      for (int u = 0; u < kBackChunks; ++u)
-        raw[u] = c + u < nch ? __ldg(reinterpret_cast<const uint4*>(Qp + ((int64_t)(c + u) * N + i) * 8))
-                             : make_uint4(0, 0, 0, 0);
-#pragma unroll
-      for (int u = 0; u < kBackChunks; ++u) {
-        if (c + u < nch) {  // uniform over the block
-          float q[8];
-          Vec16<T>::unpack(raw[u], q);
-#pragma unroll
-          for (int v = 0; v < 8; ++v) {
-            const float4* cr = reinterpret_cast<const float4*>(Cs + ((c + u) * 8 + v) * LP);
-#pragma unroll
-            for (int k4 = 0; k4 < LP / 4; ++k4) {
-              const float4 cv = cr[k4];
-              acc[4 * k4 + 0] = fmaf(q[v], cv.x, acc[4 * k4 + 0]);
-              acc[4 * k4 + 1] = fmaf(q[v], cv.y, acc[4 * k4 + 1]);
-              acc[4 * k4 + 2] = fmaf(q[v], cv.z, acc[4 * k4 + 2]);
-              acc[4 * k4 + 3] = fmaf(q[v], cv.w, acc[4 * k4 + 3]);
-            }
-          }
-        }
-      }
-    }
-    if (sl >= 0) {
-#pragma unroll
-      for (int k = 0; k < LP; ++k) acc[k] = 0.f;
-    }
-    if (xhat) {
-      float4* xo = reinterpret_cast<float4*>(xhat + i * LP);
-#pragma unroll
-      for (int k4 = 0; k4 < LP / 4; ++k4) {
-        float o[4];
-#pragma unroll
-        for (int t = 0; t < 4; ++t) {
-          const int k = 4 * k4 + t;
-          o[t] = (k >= L) ? 0.f : ((sl >= 0) ? (k == sl ? sq[i] : 0.f) : acc[k]);
-        }
-        xo[k4] = make_float4(o[0], o[1], o[2], o[3]);
-      }
-    } else {
-      const float si = s[i];
-      int best = 0;
-      float bv = -INFINITY;
-#pragma unroll
-      for (int k = 0; k < LP; ++k) {
-        if (k < L) {
-          const float u = (sl >= 0) ? (k == sl ? 1.f : 0.f) : acc[k] * si;
-          U[i * L + k] = u;
-          if (u > bv) { bv = u; best = k; }
-        }
-      }
-      if (labels) labels[i] = (uint8_t)best;
-      if (clear_seedlab && sl >= 0) clear_seedlab[i] = -1;
+  // seed rows discard the products (their flag is loaded with the first chunks)
+  if constexpr (LP <= 8) {  // (16 labels: the four-voxel form would spill)
+    if (nch <= kBackChunks / 4) {
+      backproject_rows<T, LP, 4>(Qp, N, nch, Cs, seedlab, sq, s, L, xhat, U, labels, clear_seedlab);
+      return;
     }
   }
+  if (nch <= kBackChunks / 2)
+    backproject_rows<T, LP, 2>(Qp, N, nch, Cs, seedlab, sq, s, L, xhat, U, labels, clear_seedlab);
+  else
+    backproject_rows<T, LP, 1>(Qp, N, nch, Cs, seedlab, sq, s, L, xhat, U, labels, clear_seedlab);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -3058,7 +3094,8 @@ extern "C" rw_status rw_solve(const rw_graph* g, const rw_basis* b, const int32_
     RW_LAUNCH_CHECK();
   }
   RW_TRY(mark(5));
-  // back-projection (+ refinement)
+  // back-projection (+ refinement); the 16-bit kernel holds three blocks per SM
+  const int nblk_b = fmt == RW_BASIS_F32 ? nblk : 3 * sms;
   const int steps = opts->refine_steps;
   float* xh0 = nullptr;
   float* xh1 = nullptr;
@@ -3069,11 +3106,11 @@ extern "C" rw_status rw_solve(const rw_graph* g, const rw_basis* b, const int32_
     xh1 = ws.xhat[1].as<float>();
   }
   if (fmt == RW_BASIS_F16)
-    RW_TRY(proj_back<__half>(lp, true, b->Q16, ldq_e, phat, seedlab, g, mdev, part, nblk, C, cscale, xh0, prob_dev, labels_dev, L, st, steps == 0 ? seedlab : nullptr));
+    RW_TRY(proj_back<__half>(lp, true, b->Q16, ldq_e, phat, seedlab, g, mdev, part, nblk_b, C, cscale, xh0, prob_dev, labels_dev, L, st, steps == 0 ? seedlab : nullptr));
   else if (fmt == RW_BASIS_BF16)
-    RW_TRY(proj_back<__nv_bfloat16>(lp, true, b->Qbf, ldq_e, phat, seedlab, g, mdev, part, nblk, C, cscale, xh0, prob_dev, labels_dev, L, st, steps == 0 ? seedlab : nullptr));
+    RW_TRY(proj_back<__nv_bfloat16>(lp, true, b->Qbf, ldq_e, phat, seedlab, g, mdev, part, nblk_b, C, cscale, xh0, prob_dev, labels_dev, L, st, steps == 0 ? seedlab : nullptr));
   else
-    RW_TRY(proj_back<float>(lp, true, b->Q32, ldq_e, phat, seedlab, g, mdev, part, nblk, C, cscale, xh0, prob_dev, labels_dev, L, st, steps == 0 ? seedlab : nullptr));
+    RW_TRY(proj_back<float>(lp, true, b->Q32, ldq_e, phat, seedlab, g, mdev, part, nblk_b, C, cscale, xh0, prob_dev, labels_dev, L, st, steps == 0 ? seedlab : nullptr));
   RW_TRY(mark(6));
   if (steps > 0) {
     if (opts->refine_mode == RW_REFINE_JACOBI) {
