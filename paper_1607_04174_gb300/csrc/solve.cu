@@ -9,16 +9,18 @@
 //
 // Per solve (S seeds, m_max basis columns, l labels), every kernel launched with programmatic
 // dependent launch (it waits on griddepcontrol before reading its predecessors' output):
-//   seed labels, Gaussian fit, P-hat (N x lp)      -> k_seed_scatter, k_priors (the fit from the
-//                                                     scatter blocks' sums in every block)
+//   seed labels, per-block seed statistics         -> k_seed_scatter
 //   Q_s, X = B-hat Q_n (S x m_max), r0 = L-hat_s U-hat_s + gamma U-hat_s  -> k_seed_gather
 //   K = Q_s^T X, h = Q_s^T r0, b = Q_s^T U-hat_s, G = Q_s^T Q_s (FP32)  -> k_seed_gram (cluster)
-//   m (incremental Cholesky over the nested candidates, trust region)  -> k_adapt
-//   Z = Q_n^T P-hat_n (streams the 16-bit basis once)  -> k_project_cw, k_reduce_partials
-//   (diag(lambda + gamma) - K) y = h + gamma K Lambda_gamma Z, C = y + gamma Lambda_gamma Z
-//                                                     -> k_small_solve (blocked LU)
+//   Gaussian fit, P-hat (N x lp)                    -> k_priors (beside the two before it)
+//   m (incremental Cholesky over the nested candidates, trust region) and the LU of
+//   M = diag(lambda + gamma) - K (left-looking, stopped at m)  -> k_adapt_lu (2-CTA cluster)
+//   Z = Q_n^T P-hat_n (streams the 16-bit basis once)  -> k_project_tma, k_reduce_partials
+//   C = M^{-1} (h + gamma Z)                          -> k_small_rhs (k_small_solve: pivoting)
 //   U-hat_n = Q_n C (streams the basis again)          -> k_backproject_panel
 //   refinement steps, U = s * U-hat, labels = argmax   -> k_jacobi_grid (k_jacobi_step on CSR)
+// When the cluster's shared memory does not fit, k_adapt (or k_set_m) and k_small_solve run
+// instead of k_adapt_lu and k_small_rhs.
 #include "rw_internal.cuh"
 
 #include <cooperative_groups.h>
@@ -33,7 +35,7 @@ namespace cg = cooperative_groups;
 namespace {
 
 constexpr int kMaxSmallM = 224;
-constexpr int kMaxSeeds = 65536;   // seeds per solve (the validation's limit)  // m x m FP32 factorizations live in one CTA's shared memory
+constexpr int kMaxSeeds = 65536;   // seeds per solve (the validation's limit)
 
 int lpad_of(int L) { return L <= 4 ? 4 : (L <= 8 ? 8 : 16); }
 
@@ -455,48 +457,11 @@ __device__ void gemm_trailing(float* A, int ms, int m, int ncol, int r1, int p0,
   }
 }
 
-// A[i][j] -= sum_{q < 32} A[i][p0 + q] A[p0 + q][j] for i in [i0, i1), j in [j0, j1): warp
-// tasks of RU rows x 32 NV columns (lane = column within each 32-column group)
-template <int RU, int NV>
-__device__ void gemm_rect(float* A, int ms, int i0, int i1, int j0, int j1, int p0) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const int n = i1 - i0, nc = j1 - j0;
-  if (n <= 0 || nc <= 0) return;
-  const int nrt = (n + RU - 1) / RU, nct = (nc + 32 * NV - 1) / (32 * NV);
-  for (int task = warp; task < nrt * nct; task += nw) {
-    const int ib = i0 + RU * (task / nct), jb = j0 + 32 * NV * (task % nct) + lane;
-    float acc[RU][NV];
-#pragma unroll
-    for (int u = 0; u < RU; ++u)
-#pragma unroll
-      for (int v = 0; v < NV; ++v) acc[u][v] = 0.f;
-#pragma unroll 2
-    for (int q = 0; q < 32; ++q) {
-      float av[RU], bv[NV];
-#pragma unroll
-      for (int u = 0; u < RU; ++u) av[u] = A[min(ib + u, i1 - 1) * ms + p0 + q];
-#pragma unroll
-      for (int v = 0; v < NV; ++v) bv[v] = A[(p0 + q) * ms + min(jb + 32 * v, j1 - 1)];
-#pragma unroll
-      for (int u = 0; u < RU; ++u)
-#pragma unroll
-        for (int v = 0; v < NV; ++v) acc[u][v] = fmaf(av[u], bv[v], acc[u][v]);
-    }
-#pragma unroll
-    for (int u = 0; u < RU; ++u)
-#pragma unroll
-      for (int v = 0; v < NV; ++v) {
-        const int i = ib + u, j = jb + 32 * v;
-        if (i < i1 && j < j1) A[i * ms + j] -= acc[u][v];
-      }
-  }
-}
-
-// The same update for a row stride that is a multiple of 4 and p0, j0 multiples of 4: both
-// operands move as 16-byte loads.  A warp task covers RU (32 / LC) rows x 4 LC columns: lane
-// (lr = lane / LC, lc = lane % LC) owns rows ib + lr RU + u and the four columns jb + 4 lc ..;
-// per four steps of q, RU loads of the row operand and four of the column operand feed 16 RU
-// FMAs.
+// A[i][j] -= sum_{q < 32} A[i][p0 + q] A[p0 + q][j] for i in [i0, i1), j in [j0, j1), for a row
+// stride that is a multiple of 4 and p0, j0 multiples of 4: both operands move as 16-byte
+// loads.  A warp task covers RU (32 / LC) rows x 4 LC columns: lane (lr = lane / LC,
+// lc = lane % LC) owns rows ib + lr RU + u and the four columns jb + 4 lc ..; per four steps of
+// q, RU loads of the row operand and four of the column operand feed 16 RU FMAs.
 template <int RU, int LC>
 __device__ void gemm4(float* A, int ms, int i0, int i1, int j0, int j1, int p0) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -1126,7 +1091,8 @@ k_seed_gram(const float* __restrict__ A, int lda, const float* __restrict__ B, i
 // (left-looking, "add eigenvectors and repeat") and stop at the first candidate whose worst
 // label passes the unconstrained test f = ||u_k||^2 - ||z_k[:m]||^2 <= f_max.  That candidate
 // is then checked exactly: a_k = L_m^{-T} z_k[:m] and f_k = ||u_k||^2 - ||z_k||^2 - mu0 ||a_k||^2,
-// which is the squared residual ||Q_s a_k - u_k||^2 (a^T (G + mu0 I) a = z^T z = b^T a).  If some ||a_k|| > rho the constrained minimum can only be larger, and the
+// which is the squared residual ||Q_s a_k - u_k||^2 (a^T (G + mu0 I) a = z^T z = b^T a).  If
+// some ||a_k|| > rho the constrained minimum can only be larger, and the
 // trust-region solution (Newton on 1/||a(mu)|| - 1/rho, a Cholesky of G_m + mu I per step) is
 // computed for it and, if it fails, for the following candidates.
 // ---------------------------------------------------------------------------------------
