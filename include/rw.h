@@ -204,6 +204,19 @@ rw_status rw_solve_host(const rw_graph* g, const rw_basis* b, const int32_t* see
                         const float* priors_host, const rw_solve_opts* opts, float* prob_host,
                         uint8_t* labels_host, rw_solve_info* info, void* stream);
 
+/* rw_solve_host without the final synchronization (a serving loop that pipelines solves on one
+ * stream): the copies and the solve are only enqueued on `stream`.  The host input buffers must
+ * stay valid, and prob_host / labels_host must not be read or reused for another purpose, until
+ * the stream has passed this call (cudaStreamSynchronize, or an event recorded after it); the
+ * host buffers must be pinned for the copies to stay asynchronous.  Consecutive calls on one
+ * graph must use the same stream (they share the graph's staging buffers).  Arguments, layouts
+ * and errors as rw_solve_host; with info != NULL the call synchronizes (as rw_solve). */
+rw_status rw_solve_host_async(const rw_graph* g, const rw_basis* b,
+                              const int32_t* seed_idx_host, const int32_t* seed_lab_host,
+                              int32_t S, int32_t n_labels, const float* priors_host,
+                              const rw_solve_opts* opts, float* prob_host, uint8_t* labels_host,
+                              rw_solve_info* info, void* stream);
+
 /* Reads (and clears) the graph's device status word.  Synchronizes the stream. */
 rw_status rw_last_device_status(const rw_graph* g, void* stream);
 

@@ -173,6 +173,20 @@ def rw_solve_host(g, b, seed_idx, seed_lab, n_labels, prob, labels=None, priors=
     return s, (_info_dict(info, n_labels) if want_info else None)
 
 
+def rw_solve_host_async(g, b, seed_idx, seed_lab, n_labels, prob, labels=None, priors=None,
+                        gamma=1e-3, m=0, m_step=10, eps=0.1, refine_steps=3,
+                        refine_mode=abi.RW_REFINE_JACOBI, omega=0.8,
+                        basis_format=abi.RW_BASIS_F16, prior_mode=0, stream=None):
+    """rw_solve_host without the final synchronization: the host buffers (pinned) must stay
+    valid and prob / labels unread until the stream has passed the call."""
+    o = _solve_opts(gamma, m, m_step, eps, refine_steps, refine_mode, omega, basis_format,
+                    prior_mode)
+    return _check(abi.lib().rw_solve_host_async(g, b, _p(seed_idx), _p(seed_lab), len(seed_idx),
+                                                n_labels, _p(priors), C.byref(o), _p(prob),
+                                                _p(labels), None, _stream(stream)),
+                  "rw_solve_host_async")
+
+
 def rw_last_device_status(g, stream=None):
     return abi.lib().rw_last_device_status(g, _stream(stream))
 

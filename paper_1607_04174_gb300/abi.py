@@ -97,6 +97,8 @@ PROTOTYPES = {
                        C.POINTER(rw_solve_info), P]),
     "rw_solve_host": (I32, [P, P, P, P, I32, I32, P, C.POINTER(rw_solve_opts), P, P,
                             C.POINTER(rw_solve_info), P]),
+    "rw_solve_host_async": (I32, [P, P, P, P, I32, I32, P, C.POINTER(rw_solve_opts), P, P,
+                                  C.POINTER(rw_solve_info), P]),
     "rw_last_device_status": (I32, [P, P]),
     "rw_solve_pcg": (I32, [P, P, P, I32, I32, P, D, I32, I32, D, P, P, C.POINTER(I32), P]),
     "rw_update_weights": (I32, [P, P, C.POINTER(rw_weight_update), P]),

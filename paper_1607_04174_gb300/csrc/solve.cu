@@ -3131,11 +3131,11 @@ extern "C" rw_status rw_solve(const rw_graph* g, const rw_basis* b, const int32_
   return RW_OK;
 }
 
-extern "C" rw_status rw_solve_host(const rw_graph* g, const rw_basis* b,
-                                   const int32_t* seed_idx_host, const int32_t* seed_lab_host,
-                                   int32_t S, int32_t n_labels, const float* priors_host,
-                                   const rw_solve_opts* opts, float* prob_host,
-                                   uint8_t* labels_host, rw_solve_info* info, void* stream) {
+static rw_status solve_host(const rw_graph* g, const rw_basis* b, const int32_t* seed_idx_host,
+                            const int32_t* seed_lab_host, int32_t S, int32_t n_labels,
+                            const float* priors_host, const rw_solve_opts* opts,
+                            float* prob_host, uint8_t* labels_host, rw_solve_info* info,
+                            void* stream, bool sync) {
   if (!g || !b || !seed_idx_host || !seed_lab_host || !opts || !prob_host) return RW_ERR_INVALID_ARG;
   if (S < 1 || S > 65536 || n_labels < 1 || n_labels > RW_MAX_LABELS) return RW_ERR_INVALID_ARG;
   cudaStream_t st = rw_stream(stream);
@@ -3164,8 +3164,28 @@ extern "C" rw_status rw_solve_host(const rw_graph* g, const rw_basis* b,
                                 cudaMemcpyDeviceToHost, st));
   if (labels_host)
     RW_CHECK_CUDA(cudaMemcpyAsync(labels_host, d + off_labels, g->N, cudaMemcpyDeviceToHost, st));
-  RW_CHECK_CUDA(cudaStreamSynchronize(st));
+  if (sync) RW_CHECK_CUDA(cudaStreamSynchronize(st));
   return s;
+}
+
+extern "C" rw_status rw_solve_host(const rw_graph* g, const rw_basis* b,
+                                   const int32_t* seed_idx_host, const int32_t* seed_lab_host,
+                                   int32_t S, int32_t n_labels, const float* priors_host,
+                                   const rw_solve_opts* opts, float* prob_host,
+                                   uint8_t* labels_host, rw_solve_info* info, void* stream) {
+  return solve_host(g, b, seed_idx_host, seed_lab_host, S, n_labels, priors_host, opts,
+                    prob_host, labels_host, info, stream, true);
+}
+
+extern "C" rw_status rw_solve_host_async(const rw_graph* g, const rw_basis* b,
+                                         const int32_t* seed_idx_host,
+                                         const int32_t* seed_lab_host, int32_t S,
+                                         int32_t n_labels, const float* priors_host,
+                                         const rw_solve_opts* opts, float* prob_host,
+                                         uint8_t* labels_host, rw_solve_info* info,
+                                         void* stream) {
+  return solve_host(g, b, seed_idx_host, seed_lab_host, S, n_labels, priors_host, opts,
+                    prob_host, labels_host, info, stream, false);
 }
 
 extern "C" rw_status rw_solve_priors(const rw_graph* g, const int32_t* seed_idx_dev,

@@ -217,6 +217,18 @@ def test_host_entry_point_matches_device(c1):
                          lab, m=50, refine_steps=3)
         np.testing.assert_array_equal(prob.astype(np.float64), U_dev)
         np.testing.assert_array_equal(lab, lab_dev)
+        # the asynchronous entry point, pinned buffers, several calls in flight on one stream
+        si = torch.from_numpy(c1["si"].astype(np.int32)).pin_memory()
+        sl = torch.from_numpy(c1["sl"].astype(np.int32)).pin_memory()
+        outs = [(torch.zeros(c1["g"].N, 2).pin_memory(), torch.zeros(c1["g"].N, dtype=torch.uint8).pin_memory())
+                for _ in range(3)]
+        for hp, hl in outs:
+            rw.rw_solve_host_async(g, b, si.numpy(), sl.numpy(), 2, hp.numpy(), hl.numpy(), m=50,
+                                   refine_steps=3)
+        torch.cuda.synchronize()
+        for hp, hl in outs:
+            np.testing.assert_array_equal(hp.numpy().astype(np.float64), U_dev)
+            np.testing.assert_array_equal(hl.numpy(), lab_dev)
     finally:
         rw.rw_basis_free(b)
         rw.rw_graph_free(g)
