@@ -957,7 +957,8 @@ __device__ void seed_residuals(const float* __restrict__ Qs, int ldq, const floa
   // (lanes over the columns), labels in groups of 4; the 16 (seed, label) dot products are
   // reduced across the warp by a reduce-scatter butterfly (even lane 2j holds sum j).
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  if (threadIdx.x < RW_MAX_LABELS) fk[threadIdx.x] = 0.f;
+  __shared__ float wf[8 * RW_MAX_LABELS];  // per-warp sums (8 warps), added in warp order
+  if (threadIdx.x < 8 * RW_MAX_LABELS) wf[threadIdx.x] = 0.f;
   __syncthreads();
   for (int k0 = 0; k0 < L; k0 += 4) {
     float acc = 0.f;  // lane 2j accumulates the squared residuals of entry j = 4 q + t
@@ -998,8 +999,14 @@ __device__ void seed_residuals(const float* __restrict__ Qs, int ldq, const floa
     for (int t = 0; t < 4; ++t) {
       float v = ((lane & 1) == 0 && ((lane >> 1) & 3) == t) ? acc : 0.f;
       v = warp_sum(v);
-      if (lane == 0 && k0 + t < L) atomicAdd(&fk[k0 + t], v);
+      if (lane == 0 && k0 + t < L) wf[warp * RW_MAX_LABELS + k0 + t] = v;
     }
+  }
+  __syncthreads();
+  if (threadIdx.x < L) {
+    float v = 0.f;
+    for (int w = 0; w < nw; ++w) v += wf[w * RW_MAX_LABELS + threadIdx.x];
+    fk[threadIdx.x] = v;
   }
   __syncthreads();
 }
@@ -1112,6 +1119,7 @@ __device__ void adapt_body(const float* __restrict__ G, int ldg, const float* __
   float* bb = z + (size_t)L * mmax;       // L x mmax
   float* al = bb + (size_t)L * mmax;      // L x mmax
   __shared__ float ck[RW_MAX_LABELS], zz[RW_MAX_LABELS], fk[RW_MAX_LABELS], nk[RW_MAX_LABELS];
+  __shared__ float wpart[8 * RW_MAX_LABELS + 8];  // per-warp partial sums (8 warps)
   __shared__ float dinv[kMaxSmallM];  // reciprocals of diag(L)
   __shared__ __align__(16) float colbuf[128];
   __shared__ float mu0s, red;
@@ -1137,13 +1145,24 @@ __device__ void adapt_body(const float* __restrict__ G, int ldg, const float* __
 #pragma unroll
     for (int k = 0; k < LP; ++k) {
       float v = warp_sum(acc[k]);
-      if (lane == 0 && k < L) atomicAdd(&ck[k], v);
+      if (lane == 0 && k < L) wpart[warp * RW_MAX_LABELS + k] = v;
     }
     // trace of G (for mu0): one diagonal entry per thread
     float tr = 0.f;
     for (int i = tid; i < mmax; i += blockDim.x) tr += G[(int64_t)i * ldg + i];
     tr = warp_sum(tr);
-    if (lane == 0) atomicAdd(&red, tr);
+    if (lane == 0) wpart[8 * RW_MAX_LABELS + warp] = tr;
+  }
+  __syncthreads();
+  // the warps' sums added in warp order (deterministic)
+  if (tid < L) {
+    float v = 0.f;
+    for (int w = 0; w < nw; ++w) v += wpart[w * RW_MAX_LABELS + tid];
+    ck[tid] = v;
+  } else if (tid == RW_MAX_LABELS) {
+    float v = 0.f;
+    for (int w = 0; w < nw; ++w) v += wpart[8 * RW_MAX_LABELS + w];
+    red = v;
   }
 #pragma unroll 4
   for (int e = tid; e < L * mmax; e += blockDim.x) {
