@@ -138,8 +138,13 @@ void rw_basis_free(rw_basis* b);
  *   (I - X Lambda_gamma Q_s^T) F_s = L_s U_s + gamma (U_s + X Lambda_gamma Z)      Eq. (Fs)
  *   U_n = Q_n Lambda_gamma (Q_s^T F_s + gamma Z)                           Eq. (U_lin_comb)
  * solved through the equivalent m x m system (Lambda_gamma^{-1} - Q_s^T X) y = Q_s^T rhs,
- * C = y + gamma Lambda_gamma Z, U_n = Q_n C (Woodbury form of Eq. Fs).  Then refine_steps
- * damped-Jacobi steps on Eq. (rw_eq) and hard labels = argmax (ties -> lowest label).
+ * C = y + gamma Lambda_gamma Z, U_n = Q_n C (Woodbury form of Eq. Fs); with
+ * M = Lambda_gamma^{-1} - Q_s^T X and h = Q_s^T (L_s U_s + gamma U_s) that is C = M^{-1}
+ * (h + gamma Z).  M is factored by LU without pivoting (a pivot below 1e-3 of its row's scale
+ * falls back to partial pivoting).  Then refine_steps damped-Jacobi steps on Eq. (rw_eq) and
+ * hard labels = argmax (ties -> lowest label).  m <= 224; the m x m system lives in one CTA's
+ * shared memory, so large m with many labels returns RW_ERR_UNSUPPORTED (e.g. m = 224 with 16
+ * labels; m = 200 with 16 labels and m = 224 with 4 labels are supported).
  * ---------------------------------------------------------------------------------------- */
 enum { RW_REFINE_JACOBI = 0, RW_REFINE_PCG = 1 };
 enum { RW_BASIS_F16 = 0, RW_BASIS_BF16 = 1, RW_BASIS_F32 = 2 };
@@ -163,11 +168,13 @@ typedef struct rw_solve_opts {
 
 /* Phases of one online solve, in order (indices into rw_solve_info.phase_ms). */
 enum {
-  RW_PHASE_SEEDS = 0,     /* seed scatter/validation, Gaussian fit, hat-space priors          */
-  RW_PHASE_GATHER = 1,    /* Q_s, X = B Q_n, seed-side products Q_s^T X, Q_s^T r, Q_s^T Q_s    */
-  RW_PHASE_ADAPT = 2,     /* choice of m (Eq. alpha_1)                                        */
+  RW_PHASE_SEEDS = 0,     /* seed scatter/validation                                          */
+  RW_PHASE_GATHER = 1,    /* Q_s, X = B Q_n, seed-side products Q_s^T X, Q_s^T r, Q_s^T Q_s,
+                             Gaussian fit and hat-space priors                                */
+  RW_PHASE_ADAPT = 2,     /* choice of m (Eq. alpha_1) and the factorization of the m x m
+                             matrix M (beside it)                                             */
   RW_PHASE_PROJECT = 3,   /* Z = Q_n^T P_n (one pass over the 16-bit basis)                   */
-  RW_PHASE_SMALL = 4,     /* m x m system of Eq. (Fs) in Woodbury form                        */
+  RW_PHASE_SMALL = 4,     /* C from the factors: the m x m system of Eq. (Fs), Woodbury form  */
   RW_PHASE_BACK = 5,      /* U_n = Q_n C (second pass over the basis)                         */
   RW_PHASE_REFINE = 6,    /* refinement steps, output, hard labels                            */
   RW_NUM_PHASES = 7
