@@ -1540,8 +1540,18 @@ __global__ void k_reduce_partials(const float* __restrict__ part, int nblk, int 
   if (e >= mq * lp) return;
   const int row = e / lp;
   float s = 0.f;
-  if (row < ldq)
-    for (int b = lane; b < nblk; b += 32) s += part[(int64_t)b * ldq * lp + e];
+  if (row < ldq) {  // up to 16 partials per lane requested at once, added in block order
+    for (int b0 = lane; b0 < nblk; b0 += 32 * 16) {
+      float v[16];
+#pragma unroll
+      for (int u = 0; u < 16; ++u) {
+        const int b = b0 + 32 * u;
+        v[u] = b < nblk ? part[(int64_t)b * ldq * lp + e] : 0.f;
+      }
+#pragma unroll
+      for (int u = 0; u < 16; ++u) s += v[u];
+    }
+  }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffff, s, o);
   if (lane == 0) Z[e] = s * scale;
