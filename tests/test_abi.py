@@ -80,3 +80,68 @@ def test_struct_layouts_match_c(tmp_path):
         assert int(got[s]) == C.sizeof(cls), s
         for f in fields:
             assert int(got[f"{s}.{f}"]) == getattr(cls, f).offset, f"{s}.{f}"
+
+
+def _null_args(argtypes):
+    """Integers 1, doubles 1.0, every pointer NULL."""
+    args = []
+    for t in argtypes:
+        if t in (C.c_int32, C.c_int64):
+            args.append(1)
+        elif t is C.c_double:
+            args.append(1.0)
+        else:
+            args.append(None)
+    return args
+
+
+def test_null_handles_are_refused_on_the_host(lib):
+    """Every entry point that returns a status checks its arguments before any device work:
+    with NULL handles and buffers it returns RW_ERR_INVALID_ARG and launches nothing (the
+    library's launch counter stays put).  The accessors and destructors accept NULL."""
+    from paper_1607_04174_gb300 import abi
+    before = lib.rw_kernel_launches()
+    status_calls = [n for n, (res, _) in abi.PROTOTYPES.items()
+                    if res is C.c_int32 and n != "rw_basis_m"]
+    assert len(status_calls) >= 17
+    for name in status_calls:
+        st = getattr(lib, name)(*_null_args(abi.PROTOTYPES[name][1]))
+        assert st == -1, (name, st)
+    assert lib.rw_basis_m(None) == 0
+    assert lib.rw_graph_num_nodes(None) == 0
+    lib.rw_graph_free(None)
+    lib.rw_basis_free(None)
+    assert lib.rw_kernel_launches() == before
+    # every declared entry point is one of the calls above or an accessor checked elsewhere
+    covered = set(status_calls) | {"rw_basis_m", "rw_graph_num_nodes", "rw_graph_free",
+                                   "rw_basis_free", "rw_status_str", "rw_last_error_message",
+                                   "rw_kernel_launches"}
+    assert set(_declared()) <= covered, sorted(set(_declared()) - covered)
+
+
+@pytest.mark.parametrize("field,value", [("ndim", 1), ("ndim", 4), ("beta", -1.0),
+                                         ("beta", float("nan")), ("weight_form", 7),
+                                         ("dims0", 0), ("dims2", 0), ("huge", None)])
+def test_invalid_graph_descriptors_are_refused(lib, field, value):
+    """rw_build_graph rejects a bad descriptor before it touches the image or the device
+    (the image pointer below is a host address that is never read) and clears *out."""
+    from paper_1607_04174_gb300 import abi
+    import numpy as np
+    desc = abi.rw_graph_desc()
+    desc.ndim, desc.beta, desc.weight_form, desc.normalized = 3, 90.0, 0, 1
+    desc.dims[0], desc.dims[1], desc.dims[2] = 8, 8, 8
+    if field == "dims0":
+        desc.dims[0] = value
+    elif field == "dims2":
+        desc.dims[2] = value
+    elif field == "huge":  # N = 2^33 nodes does not fit the 32-bit node index
+        desc.dims[0], desc.dims[1], desc.dims[2] = 2048, 2048, 2048
+    else:
+        setattr(desc, field, value)
+    image = np.zeros(4, np.float32)
+    out = C.c_void_p(12345)
+    before = lib.rw_kernel_launches()
+    st = lib.rw_build_graph(C.byref(desc), image.ctypes.data, None, C.byref(out))
+    assert st == -1
+    assert out.value is None
+    assert lib.rw_kernel_launches() == before
