@@ -212,7 +212,7 @@ NCU_DRAM_BYTES = {"k_adapt_lu": 361301}
 
 PHASE_KERNELS = {"seeds": "k_seed_scatter",
                  "gather": "k_seed_gather+k_seed_gram+k_priors", "adapt": "k_adapt_lu",
-                 "project": "k_project_cw+k_reduce_partials", "small": "k_small_rhs",
+                 "project": "k_project_tma+k_reduce_partials", "small": "k_small_rhs",
                  "back": "k_backproject_panel", "refine": "k_jacobi_grid x3"}
 
 
