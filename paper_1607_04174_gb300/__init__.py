@@ -29,16 +29,28 @@ def _check(s, what):
     return s
 
 
-def _p(x):
-    if x is None:
-        return None
-    if isinstance(x, int):
+def _dp(x):
+    """Address of a device buffer: a CUDA tensor, an integer address or None.  Host memory
+    (a NumPy array or a CPU tensor) is refused here rather than handed to a kernel."""
+    if x is None or isinstance(x, int):
+        return x
+    if isinstance(x, np.ndarray) or not getattr(x, "is_cuda", False):
+        raise ValueError("a device buffer (CUDA tensor) is expected here, not host memory")
+    return x.data_ptr()
+
+
+def _hp(x):
+    """Address of a host buffer: a C-contiguous NumPy array, a CPU tensor, an integer address
+    or None.  A CUDA tensor is refused (the host entry points copy from and to host memory)."""
+    if x is None or isinstance(x, int):
         return x
     if isinstance(x, np.ndarray):
         if not x.flags["C_CONTIGUOUS"]:
             raise ValueError("host arrays must be C-contiguous")
         return x.ctypes.data
-    return x.data_ptr()  # torch tensor
+    if getattr(x, "is_cuda", False):
+        raise ValueError("a host buffer is expected here, not a CUDA tensor")
+    return x.data_ptr()
 
 
 def _stream(stream):
@@ -73,7 +85,7 @@ def rw_build_graph(J, dims, beta, weight_form=abi.RW_WEIGHT_SQ, normalized=True,
     d.weight_form = int(weight_form)
     d.normalized = 1 if normalized else 0
     h = C.c_void_p()
-    _check(abi.lib().rw_build_graph(C.byref(d), _p(J), _stream(stream), C.byref(h)),
+    _check(abi.lib().rw_build_graph(C.byref(d), _dp(J), _stream(stream), C.byref(h)),
            "rw_build_graph")
     return h.value
 
@@ -87,12 +99,12 @@ def rw_graph_num_nodes(g):
 
 
 def rw_graph_weights(g, w=None, d=None, stream=None):
-    return _check(abi.lib().rw_graph_weights(g, _p(w), _p(d), _stream(stream)), "rw_graph_weights")
+    return _check(abi.lib().rw_graph_weights(g, _dp(w), _dp(d), _stream(stream)), "rw_graph_weights")
 
 
 def rw_apply_laplacian(g, X, Y, k=None, stream=None):
     k = X.shape[1] if k is None else k
-    return _check(abi.lib().rw_apply_laplacian(g, _p(X), _ld(X), _p(Y), _ld(Y), k,
+    return _check(abi.lib().rw_apply_laplacian(g, _dp(X), _ld(X), _dp(Y), _ld(Y), k,
                                                _stream(stream)), "rw_apply_laplacian")
 
 
@@ -110,7 +122,7 @@ def rw_precompute(g, m, guard=-1, max_iter=0, tol=0.0, cheb_degree=-1, seed=0, s
 def rw_basis_create(g, Q, lam, stream=None):
     lam = np.ascontiguousarray(lam, dtype=np.float64)
     h = C.c_void_p()
-    _check(abi.lib().rw_basis_create(g, Q.shape[1], _p(Q),
+    _check(abi.lib().rw_basis_create(g, Q.shape[1], _dp(Q),
                                      lam.ctypes.data_as(C.POINTER(C.c_double)), _stream(stream),
                                      C.byref(h)), "rw_basis_create")
     return h.value
@@ -122,7 +134,7 @@ def rw_basis_m(b):
 
 def rw_basis_get(b, Q=None, stream=None):
     lam = np.zeros(rw_basis_m(b))
-    _check(abi.lib().rw_basis_get(b, _p(Q), lam.ctypes.data_as(C.POINTER(C.c_double)),
+    _check(abi.lib().rw_basis_get(b, _dp(Q), lam.ctypes.data_as(C.POINTER(C.c_double)),
                                   _stream(stream)), "rw_basis_get")
     return lam
 
@@ -152,8 +164,8 @@ def rw_solve(g, b, seed_idx, seed_lab, n_labels, prob, labels=None, priors=None,
     o = _solve_opts(gamma, m, m_step, eps, refine_steps, refine_mode, omega, basis_format,
                     prior_mode, 1 if record_phases else 0)
     info = abi.rw_solve_info()
-    s = _check(abi.lib().rw_solve(g, b, _p(seed_idx), _p(seed_lab), len(seed_idx), n_labels,
-                                  _p(priors), C.byref(o), _p(prob), _p(labels),
+    s = _check(abi.lib().rw_solve(g, b, _dp(seed_idx), _dp(seed_lab), len(seed_idx), n_labels,
+                                  _dp(priors), C.byref(o), _dp(prob), _dp(labels),
                                   C.byref(info) if want_info else None, _stream(stream)),
                "rw_solve")
     return s, (_info_dict(info, n_labels) if want_info else None)
@@ -166,8 +178,8 @@ def rw_solve_host(g, b, seed_idx, seed_lab, n_labels, prob, labels=None, priors=
     o = _solve_opts(gamma, m, m_step, eps, refine_steps, refine_mode, omega, basis_format,
                     prior_mode)
     info = abi.rw_solve_info()
-    s = _check(abi.lib().rw_solve_host(g, b, _p(seed_idx), _p(seed_lab), len(seed_idx),
-                                       n_labels, _p(priors), C.byref(o), _p(prob), _p(labels),
+    s = _check(abi.lib().rw_solve_host(g, b, _hp(seed_idx), _hp(seed_lab), len(seed_idx),
+                                       n_labels, _hp(priors), C.byref(o), _hp(prob), _hp(labels),
                                        C.byref(info) if want_info else None, _stream(stream)),
                "rw_solve_host")
     return s, (_info_dict(info, n_labels) if want_info else None)
@@ -181,9 +193,9 @@ def rw_solve_host_async(g, b, seed_idx, seed_lab, n_labels, prob, labels=None, p
     valid and prob / labels unread until the stream has passed the call."""
     o = _solve_opts(gamma, m, m_step, eps, refine_steps, refine_mode, omega, basis_format,
                     prior_mode)
-    return _check(abi.lib().rw_solve_host_async(g, b, _p(seed_idx), _p(seed_lab), len(seed_idx),
-                                                n_labels, _p(priors), C.byref(o), _p(prob),
-                                                _p(labels), None, _stream(stream)),
+    return _check(abi.lib().rw_solve_host_async(g, b, _hp(seed_idx), _hp(seed_lab), len(seed_idx),
+                                                n_labels, _hp(priors), C.byref(o), _hp(prob),
+                                                _hp(labels), None, _stream(stream)),
                   "rw_solve_host_async")
 
 
@@ -194,8 +206,8 @@ def rw_last_device_status(g, stream=None):
 def rw_solve_pcg(g, seed_idx, seed_lab, n_labels, prob, labels=None, priors=None, gamma=1e-3,
                  prior_mode=0, iters=1000, tol=0.0, want_iters=True, stream=None):
     it = C.c_int32(0)
-    _check(abi.lib().rw_solve_pcg(g, _p(seed_idx), _p(seed_lab), len(seed_idx), n_labels,
-                                  _p(priors), gamma, prior_mode, iters, tol, _p(prob), _p(labels),
+    _check(abi.lib().rw_solve_pcg(g, _dp(seed_idx), _dp(seed_lab), len(seed_idx), n_labels,
+                                  _dp(priors), gamma, prior_mode, iters, tol, _dp(prob), _dp(labels),
                                   C.byref(it) if want_iters else None, _stream(stream)),
            "rw_solve_pcg")
     return it.value if want_iters else None
@@ -209,8 +221,8 @@ def rw_update_weights(g, b, kind, beta=0.0, roi_lo=(0, 0, 0), roi_hi=(1, 1, 1), 
     for i in range(3):
         u.roi_lo[i] = roi_lo[i] if i < len(roi_lo) else 0
         u.roi_hi[i] = roi_hi[i] if i < len(roi_hi) else 1
-    u.edge_ids_dev = _p(edge_ids)
-    u.edge_w_dev = _p(edge_w)
+    u.edge_ids_dev = _dp(edge_ids)
+    u.edge_w_dev = _dp(edge_w)
     u.n_edges = 0 if edge_ids is None else len(edge_ids)
     return _check(abi.lib().rw_update_weights(g, b, C.byref(u), _stream(stream)),
                   "rw_update_weights")
@@ -221,13 +233,13 @@ def rw_update_topology(g, b, kind, edge_ids=None, n_bar=0, eta_rowptr=None, eta_
     u = abi.rw_topology_update()
     u.kind = kind
     u.naive = 1 if naive else 0
-    u.edge_ids_dev = _p(edge_ids)
+    u.edge_ids_dev = _dp(edge_ids)
     u.n_edges = 0 if edge_ids is None else len(edge_ids)
     u.n_bar = n_bar
-    u.eta_rowptr_dev = _p(eta_rowptr)
-    u.eta_col_dev = _p(eta_col)
-    u.eta_val_dev = _p(eta_val)
-    u.etabar_val_dev = _p(etabar_val)
+    u.eta_rowptr_dev = _dp(eta_rowptr)
+    u.eta_col_dev = _dp(eta_col)
+    u.eta_val_dev = _dp(eta_val)
+    u.etabar_val_dev = _dp(etabar_val)
     ga, ba = C.c_void_p(), C.c_void_p()
     s = _check(abi.lib().rw_update_topology(g, b, C.byref(u), _stream(stream), C.byref(ga),
                                             C.byref(ba)), "rw_update_topology")
@@ -237,30 +249,30 @@ def rw_update_topology(g, b, kind, edge_ids=None, n_bar=0, eta_rowptr=None, eta_
 def rw_grad_exact(g, seed_idx, seed_lab, n_labels, priors, gamma, U, dloss_dU, grad_w,
                   rel_tol=1e-7, max_iter=20000, stream=None):
     gb = C.c_double(0.0)
-    _check(abi.lib().rw_grad_exact(g, _p(seed_idx), _p(seed_lab), len(seed_idx), n_labels,
-                                   _p(priors), gamma, _p(U), _p(dloss_dU), rel_tol, max_iter,
-                                   _p(grad_w), C.byref(gb), _stream(stream)), "rw_grad_exact")
+    _check(abi.lib().rw_grad_exact(g, _dp(seed_idx), _dp(seed_lab), len(seed_idx), n_labels,
+                                   _dp(priors), gamma, _dp(U), _dp(dloss_dU), rel_tol, max_iter,
+                                   _dp(grad_w), C.byref(gb), _stream(stream)), "rw_grad_exact")
     return gb.value
 
 
 def rw_grad_fast(g, b, seed_idx, seed_lab, n_labels, priors, gamma, m, dloss_dU, grad_w,
                  refine_steps=3, omega=0.8, U_out=None, stream=None):
     gb = C.c_double(0.0)
-    _check(abi.lib().rw_grad_fast(g, b, _p(seed_idx), _p(seed_lab), len(seed_idx), n_labels,
-                                  _p(priors), gamma, m, refine_steps, omega, _p(dloss_dU),
-                                  _p(U_out), _p(grad_w), C.byref(gb), _stream(stream)),
+    _check(abi.lib().rw_grad_fast(g, b, _dp(seed_idx), _dp(seed_lab), len(seed_idx), n_labels,
+                                  _dp(priors), gamma, m, refine_steps, omega, _dp(dloss_dU),
+                                  _dp(U_out), _dp(grad_w), C.byref(gb), _stream(stream)),
            "rw_grad_fast")
     return gb.value
 
 
 def rw_solve_priors(g, seed_idx, seed_lab, n_labels, priors, stream=None):
-    return _check(abi.lib().rw_solve_priors(g, _p(seed_idx), _p(seed_lab), len(seed_idx),
-                                            n_labels, _p(priors), _stream(stream)),
+    return _check(abi.lib().rw_solve_priors(g, _dp(seed_idx), _dp(seed_lab), len(seed_idx),
+                                            n_labels, _dp(priors), _stream(stream)),
                   "rw_solve_priors")
 
 
 def rw_rayleigh_quotients_noalloc(g, Q, lam_out, m=None, stream=None):
     m = Q.shape[1] if m is None else m
-    return _check(abi.lib().rw_rayleigh_quotients_noalloc(g, _p(Q), _ld(Q), m, _p(lam_out),
+    return _check(abi.lib().rw_rayleigh_quotients_noalloc(g, _dp(Q), _ld(Q), m, _dp(lam_out),
                                                           _stream(stream)),
                   "rw_rayleigh_quotients_noalloc")

@@ -145,3 +145,38 @@ def test_invalid_graph_descriptors_are_refused(lib, field, value):
     assert st == -1
     assert out.value is None
     assert lib.rw_kernel_launches() == before
+
+
+class _FakeCudaTensor:
+    """Stands in for a CUDA tensor (no GPU here): only the two attributes the binding reads."""
+    is_cuda = True
+
+    def data_ptr(self):
+        return 0x1000
+
+
+def test_binding_refuses_the_wrong_kind_of_memory(lib):
+    """Device entry points refuse host memory (NumPy arrays, CPU tensors) and the host entry
+    points refuse CUDA tensors, in the binding, before the library is called."""
+    import numpy as np
+    import torch
+
+    import paper_1607_04174_gb300 as rw
+    before = lib.rw_kernel_launches()
+    si, sl = np.zeros(4, np.int32), np.zeros(4, np.int32)
+    prob = np.zeros((8, 2), np.float32)
+    with pytest.raises(ValueError, match="device buffer"):
+        rw.rw_solve(1, 1, si, sl, 2, prob)
+    with pytest.raises(ValueError, match="device buffer"):
+        rw.rw_solve(1, 1, torch.from_numpy(si), torch.from_numpy(sl), 2, torch.from_numpy(prob))
+    with pytest.raises(ValueError, match="device buffer"):
+        rw.rw_build_graph(np.zeros(16, np.float32), (4, 4), 1.0)
+    with pytest.raises(ValueError, match="device buffer"):
+        rw.rw_solve_pcg(1, torch.from_numpy(si), torch.from_numpy(sl), 2, prob)
+    with pytest.raises(ValueError, match="host buffer"):
+        rw.rw_solve_host(1, 1, si, sl, 2, _FakeCudaTensor())
+    with pytest.raises(ValueError, match="host buffer"):
+        rw.rw_solve_host_async(1, 1, _FakeCudaTensor(), sl, 2, prob)
+    with pytest.raises(ValueError, match="C-contiguous"):
+        rw.rw_solve_host(1, 1, si, sl, 2, np.zeros((2, 8), np.float32).T)
+    assert lib.rw_kernel_launches() == before
