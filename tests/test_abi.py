@@ -180,3 +180,15 @@ def test_binding_refuses_the_wrong_kind_of_memory(lib):
     with pytest.raises(ValueError, match="C-contiguous"):
         rw.rw_solve_host(1, 1, si, sl, 2, np.zeros((2, 8), np.float32).T)
     assert lib.rw_kernel_launches() == before
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    """Without the built library every call raises ImportError: there is no CPU fallback."""
+    from paper_1607_04174_gb300 import abi
+    import paper_1607_04174_gb300 as rw
+    monkeypatch.setattr(abi, "LIB_PATH", str(tmp_path / "librwgb.so"))
+    monkeypatch.setattr(abi, "_lib", None)
+    with pytest.raises(ImportError, match="missing"):
+        rw.rw_kernel_launches()
+    with pytest.raises(ImportError, match="missing"):
+        rw.rw_status_str(0)
