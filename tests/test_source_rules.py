@@ -1,0 +1,61 @@
+"""Static checks of the CUDA sources (CPU): every wait a kernel spins on is bounded, no kernel
+traps or asserts on the device, kernels with grid-wide barriers are launched cooperatively, and
+the build targets sm_103a only."""
+import os
+import re
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+CSRC = os.path.join(ROOT, "paper_1607_04174_gb300", "csrc")
+
+
+def _sources():
+    out = {}
+    for f in sorted(os.listdir(CSRC)):
+        if f.endswith((".cu", ".cuh")):
+            out[f] = open(os.path.join(CSRC, f)).read()
+    return out
+
+
+def _strip_comments(text):
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return re.sub(r"//[^\n]*", "", text)
+
+
+def test_mbarrier_waits_are_bounded():
+    """The only mbarrier poll is mbar_try_wait, and its only caller is the bounded loop that
+    gives up (setting a timeout status) after a fixed number of polls."""
+    src = {f: _strip_comments(t) for f, t in _sources().items()}
+    polls = [f for f, t in src.items() for _ in re.finditer(r"mbarrier\.try_wait", t)]
+    assert polls == ["solve.cu"]
+    uses = re.findall(r"\bmbar_try_wait\s*\(", src["solve.cu"])
+    assert len(uses) == 2  # its definition and the call inside mbar_wait_bounded
+    i = src["solve.cu"].index("void mbar_wait_bounded(")
+    body = src["solve.cu"][i:src["solve.cu"].index("\n}\n", i)]
+    assert "mbar_try_wait(" in body and "RW_DEV_TIMEOUT" in body and "return;" in body
+    assert re.search(r"it\s*>\s*\(1\s*<<\s*\d+\)", body)
+
+
+def test_no_device_traps_or_asserts():
+    for f, t in _sources().items():
+        t = _strip_comments(t)
+        assert "__trap" not in t, f
+        assert not re.search(r"(?<![A-Za-z_])assert\s*\(", t), f
+
+
+def test_grid_barrier_kernels_launch_cooperatively():
+    checked = set()
+    for f, t in _sources().items():
+        t = _strip_comments(t)
+        for m in re.finditer(r"this_grid\(\)", t):
+            head = t[:m.start()]
+            k = head.rfind("__global__")
+            name = re.search(r"\b(k_[a-z0-9_]+)\s*\(", head[k:]).group(1)
+            assert re.search(r"cudaLaunchCooperativeKernel\(\(void\*\)\s*" + name + r"\b", t), \
+                (f, name)
+            checked.add(name)
+    assert {"k_jacobi", "k_pcg"} <= checked, checked
+
+
+def test_build_targets_sm_103a_only():
+    from paper_1607_04174_gb300 import build
+    assert build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
