@@ -138,3 +138,29 @@ def test_gaussian_priors_match_normal_pdf():
     pdf = np.stack([norm.pdf(J, mu[k], sd[k]) for k in range(2)], axis=1)
     np.testing.assert_allclose(P, pdf / pdf.sum(axis=1, keepdims=True), rtol=1e-10)
     np.testing.assert_allclose(P.sum(axis=1), 1.0, atol=1e-15)
+
+
+def test_gaussian_priors_degenerate_cases():
+    """Special cases of the per-label Gaussian fit (Sec. IV-A): a label whose seeds share one
+    intensity gets the floor sigma = 1e-3 (the fit's sample deviation is 0); a voxel far from
+    every mean, where each density underflows in double precision, still gets a normalised
+    prior, one-hot on the label with the largest log-density; a label without seeds is an
+    error."""
+    from scipy.stats import norm
+    J = np.array([0.2, 0.2, 0.2, 0.7, 0.8, 0.9, 0.5, 50.0])
+    si = np.arange(6)
+    sl = np.array([0, 0, 0, 1, 1, 1], np.int32)
+    mu, sig = priors.gaussian_fit(J, si, sl, 2)
+    assert mu[0] == pytest.approx(0.2) and sig[0] == priors.SIGMA_FLOOR
+    assert mu[1] == pytest.approx(0.8) and sig[1] == pytest.approx(np.sqrt(2 / 300))
+    P = priors.gaussian_priors(J, si, sl, 2)
+    assert np.all(np.isfinite(P)) and np.allclose(P.sum(axis=1), 1.0, atol=1e-15)
+    # ordinary voxels: the normal densities with the floored deviation, normalised
+    pdf = np.stack([norm.pdf(J[:7], mu[k], sig[k]) for k in range(2)], axis=1)
+    np.testing.assert_allclose(P[:7], pdf / pdf.sum(axis=1, keepdims=True), rtol=1e-9, atol=1e-300)
+    # J = 50: both densities are 0 in double precision; the log-densities decide
+    assert norm.pdf(50.0, mu[0], sig[0]) == 0.0 and norm.pdf(50.0, mu[1], sig[1]) == 0.0
+    logd = norm.logpdf(50.0, mu, sig)
+    assert np.argmax(P[7]) == np.argmax(logd) == 1 and P[7, 1] == 1.0
+    with pytest.raises(ValueError):
+        priors.gaussian_fit(J, si, np.zeros(6, np.int32), 2)
