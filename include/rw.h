@@ -13,8 +13,11 @@
  *   `ld` elements apart.
  * - Pointers named *_dev are CUDA device pointers owned by the caller (e.g. from PyTorch);
  *   *_host are host pointers.  `stream` is a cudaStream_t (NULL = legacy default stream); all
- *   device work is enqueued on it.  The library owns only its opaque handles and the scratch
- *   memory it keeps inside them (allocated with cudaMalloc on first use, freed with the handle).
+ *   device work is enqueued on it.  The library owns its opaque handles and the scratch
+ *   memory it keeps inside them (allocated with cudaMalloc on first use, freed with the handle),
+ *   plus one fixed file-scope device array used only by rw_rayleigh_quotients_noalloc (about
+ *   2 MiB on every GPU that loads the library); calls of that entry point that overlap on the
+ *   GPU race on the array.
  * - Calls that share a handle must not run concurrently on different streams: they share the
  *   handle's scratch memory.
  * - Every call returns an rw_status.  On an error the outputs are unspecified and the handles
@@ -337,10 +340,12 @@ rw_status rw_grad_fast(const rw_graph* g, const rw_basis* b, const int32_t* seed
  * Rayleigh quotients of caller columns with no device allocation.  The paper has no
  * counterpart; this serves callers that cannot allocate device memory during a call (a host
  * application that owns the whole device memory budget through its own pool, or a thread that
- * must not enter the allocator).  It returns the same values as the value update of
- * Sec. III-B with unchanged weights: lambda_dev[i] = sum_e w_e (q_i(a) s_a - q_i(b) s_b)^2 /
- * ||q_i||^2 for the m columns of Q_dev (N x m node-major, pitch ldq a multiple of 4, >= m,
- * 16-byte aligned) under g's current weights; lambda_dev holds m doubles on the device.
+ * must not enter the allocator).  It returns the same values that rw_update_weights with
+ * RW_UPDATE_BETA and an unchanged beta leaves in the basis: lambda_dev[i] =
+ * sum_e w_e (q_i(a) s_a - q_i(b) s_b)^2 / ||q_i||^2 for the m columns of Q_dev (N x m
+ * node-major, pitch ldq a multiple of 4, >= m, 16-byte aligned) under g's current weights;
+ * lambda_dev holds m doubles on the device.  The device g was built on must be current
+ * (RW_ERR_INVALID_ARG otherwise).
  * Scratch: a fixed device array inside the library (about 2 MiB, held by every GPU that loads
  * the library until exit), no cudaMalloc or cudaFree.  The first call on a device looks up the
  * array's device address (cudaGetSymbolAddress); make that first call before any stream

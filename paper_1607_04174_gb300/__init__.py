@@ -272,7 +272,16 @@ def rw_solve_priors(g, seed_idx, seed_lab, n_labels, priors, stream=None):
 
 
 def rw_rayleigh_quotients_noalloc(g, Q, lam_out, m=None, stream=None):
+    import torch
     m = Q.shape[1] if m is None else m
+    if Q.dtype != torch.float32 or Q.dim() != 2 or Q.stride(1) != 1:
+        raise ValueError("Q must be a 2-D float32 tensor with unit column stride")
+    if Q.shape[0] != abi.lib().rw_graph_num_nodes(g):
+        raise ValueError("Q must have one row per graph node")
+    if not 1 <= m <= Q.shape[1]:
+        raise ValueError("m must be in [1, Q.shape[1]]")
+    if lam_out.dtype != torch.float64 or not lam_out.is_contiguous() or lam_out.numel() < m:
+        raise ValueError("lam_out must be a contiguous float64 tensor of at least m entries")
     return _check(abi.lib().rw_rayleigh_quotients_noalloc(g, _dp(Q), _ld(Q), m, _dp(lam_out),
                                                           _stream(stream)),
                   "rw_rayleigh_quotients_noalloc")

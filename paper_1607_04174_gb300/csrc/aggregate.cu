@@ -570,6 +570,7 @@ rw_status rw_aggregate(rw_graph* g, rw_basis* b, const rw_topology_update* u, cu
   if (!gb) return RW_ERR_OOM;
   auto fail = [&](rw_status s) { rw_graph_free(gb); return s; };
   gb->kind = RW_GRAPH_CSR;
+  gb->device = g->device;
   gb->ndim = 1;
   gb->dims[0] = nbar; gb->dims[1] = 1; gb->dims[2] = 1;
   gb->N = nbar;

@@ -335,6 +335,7 @@ extern "C" rw_status rw_build_graph(const rw_graph_desc* desc, const float* J_de
   cudaStream_t st = rw_stream(stream);
   rw_graph* g = new (std::nothrow) rw_graph();
   if (!g) return RW_ERR_OOM;
+  if (cudaGetDevice(&g->device) != cudaSuccess) g->device = 0;
   g->kind = RW_GRAPH_GRID;
   g->ndim = desc->ndim;
   g->dims[0] = desc->dims[0]; g->dims[1] = desc->dims[1]; g->dims[2] = dz;

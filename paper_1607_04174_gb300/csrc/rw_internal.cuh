@@ -135,6 +135,7 @@ struct rw_graph {
   float* sq = nullptr;    // d^{1/2} (normalized) or 1
   int* status = nullptr;  // device status word
   double dsum = 0.0;      // sum of degrees (1^T D 1)
+  int device = 0;         // CUDA device current when the handle was built
   SolveWorkspace ws;
   DevBuf upd;             // update scratch
 };

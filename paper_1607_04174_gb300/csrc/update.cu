@@ -563,6 +563,10 @@ namespace {
 constexpr int kNoAllocBlocks = 256;            // blocks of the partial-sum kernel
 constexpr int kNoAllocWidth = 32 * 4 * 8;      // columns of one partial row (m <= 1024)
 constexpr size_t kNoAllocDoubles = (size_t)kNoAllocBlocks * kNoAllocWidth + kNoAllocWidth;
+static_assert(kNoAllocWidth >= RW_NOALLOC_MAX_M,
+              "a partial row of the no-allocation scratch must hold RW_NOALLOC_MAX_M columns");
+#define RW_STR_(x) #x
+#define RW_STR(x) RW_STR_(x)
 }  // namespace
 
 static __device__ __align__(256) double g_noalloc_scratch[kNoAllocDoubles];
@@ -577,7 +581,8 @@ extern "C" rw_status rw_rayleigh_quotients_noalloc(const rw_graph* g, const floa
                                                    void* stream) {
   if (!g || !Q_dev || !lambda_dev) return RW_ERR_INVALID_ARG;
   if (m < 1 || m > RW_NOALLOC_MAX_M) {
-    rw_set_error_message("rw_rayleigh_quotients_noalloc: m must be in [1, 1024]");
+    rw_set_error_message("rw_rayleigh_quotients_noalloc: m must be in [1, "
+                         RW_STR(RW_NOALLOC_MAX_M) "]");
     return RW_ERR_INVALID_ARG;
   }
   if (ldq < m || (ldq & 3) || (reinterpret_cast<uintptr_t>(Q_dev) & 15)) {
@@ -587,7 +592,15 @@ extern "C" rw_status rw_rayleigh_quotients_noalloc(const rw_graph* g, const floa
   }
   int dev = 0;
   RW_CHECK_CUDA(cudaGetDevice(&dev));
-  if (dev < 0 || dev >= 128) return RW_ERR_UNSUPPORTED;
+  if (dev < 0 || dev >= 128) {
+    rw_set_error_message("rw_rayleigh_quotients_noalloc: device ordinals above 127 are not "
+                         "supported");
+    return RW_ERR_UNSUPPORTED;
+  }
+  if (dev != g->device) {
+    rw_set_error_message("rw_rayleigh_quotients_noalloc: the graph's device must be current");
+    return RW_ERR_INVALID_ARG;
+  }
   double* scratch = nullptr;
   {
     std::lock_guard<std::mutex> lock(g_noalloc_mu);
