@@ -44,6 +44,27 @@ METRIC = "online RW label maps/s at 512² & 128³ vs plain PCG on GPU, ≤1e-3 p
 WORKLOAD = "rwis-512x512-4label-voronoi"
 L2_FLUSH_BYTES = 256 << 20
 SEED_POOL = 400
+BETA_NEW = 150.0
+HBM_FALLBACK = 6800.0
+
+
+def stencil_bytes_per_node(k, ndim):
+    """Y = L-hat X on k columns: read the X row, write the Y row, the ndim forward-edge
+    coefficients (normalized form: no diagonal array)."""
+    return 8 * k + 4 * ndim
+
+
+def pcg_bytes_per_node(lp, ndim):
+    """One iteration of the two-pass PCG kernel: pass A reads r and the previous p, writes p
+    and q, reads the ndim coefficients and the seed flag; pass B reads x, r, p, q and writes
+    x, r (lp floats per row)."""
+    return 4 * lp * 10 + 4 * ndim + 4
+
+
+def pcg_roofline(N, lp, ndim, ms_per_iter, hbm):
+    byts = N * pcg_bytes_per_node(lp, ndim)
+    ach = byts / (ms_per_iter * 1e-3) / 1e9
+    return {"bytes_per_iteration": byts, "achieved_gbs": ach, "peak": hbm, "frac": ach / hbm}
 
 
 def seed_sets(truth, dims, count, base):
@@ -131,16 +152,35 @@ def time_oracle(n_solves, budget_s=25.0):
     from oracle import pipeline
     J, dims, truth, g, Q, lam = oracle_problem()
     sets = seed_sets(truth, dims, n_solves, synth.BASE_SEED + 101)
-    times = []
+    times, ms = [], []
     t_start = time.perf_counter()
     for si, sl in sets:
         t0 = time.perf_counter()
-        pipeline.online_solve(g, Q, lam, si, sl, LABELS, gamma=GAMMA, m=0, m_step=M_STEP,
-                              eps=EPS, refine_steps=REFINE)
+        r = pipeline.online_solve(g, Q, lam, si, sl, LABELS, gamma=GAMMA, m=0, m_step=M_STEP,
+                                  eps=EPS, refine_steps=REFINE)
         times.append(time.perf_counter() - t0)
+        ms.append(int(r["m"]))
         if time.perf_counter() - t_start > budget_s:
             break
-    return times
+    return times, ms
+
+
+def time_oracle_on(J, dims, Q, lam, sets, budget_s=25.0):
+    """The oracle's online solve (adaptive m, 3 refinement steps) on a given basis; returns
+    the per-solve times and the m it chose for each seed set."""
+    from oracle import graph, pipeline
+    g = graph.build_graph(np.asarray(J, dtype=np.float32).astype(np.float64), dims, BETA)
+    times, ms = [], []
+    t_start = time.perf_counter()
+    for si, sl in sets:
+        t0 = time.perf_counter()
+        r = pipeline.online_solve(g, Q, lam, si, sl, LABELS, gamma=GAMMA, m=0, m_step=M_STEP,
+                                  eps=EPS, refine_steps=REFINE)
+        times.append(time.perf_counter() - t0)
+        ms.append(int(r["m"]))
+        if time.perf_counter() - t_start > budget_s:
+            break
+    return times, ms
 
 
 def cpu_cores():
@@ -157,7 +197,7 @@ def reference_arm(args):
         return 0
     for _ in range(max(0, min(args.warmup, 1))):
         time_oracle(1)
-    times = time_oracle(args.steps, budget_s=240.0)
+    times, m_used = time_oracle(args.steps, budget_s=240.0)
     ms = 1000.0 * float(np.mean(times))
     value = 1000.0 / ms
     line = {
@@ -167,8 +207,9 @@ def reference_arm(args):
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "size": [SIZE, SIZE], "labels": LABELS,
                    "seeds_per_label": SEEDS_PER_LABEL, "m_max": M, "refine_steps": REFINE,
-                   "basis": "DCT columns with Rayleigh-quotient values (oracle eigensolver is "
-                            "offline-only at this size)"},
+                   "basis": "DCT columns with Rayleigh-quotient values (the oracle's "
+                            "shift-invert eigensolver takes minutes at this size)",
+                   "m_used_mean": float(np.mean(m_used))},
         "cpu_baseline": {"value": value, "unit": "label_maps/s", "cores": cpu_cores(),
                          "kind": "oracle",
                          "sample": f"{len(times)} full 512x512 online solves"},
@@ -292,10 +333,11 @@ def equal_accuracy(rw, g, b, dsets, conv, tmp, labels, flush, stream, kw, pcg_ms
             "pcg_label_maps_per_s": 1000.0 / pcg_ms, "speedup_vs_pcg": pcg_ms / ms}
 
 
-def c3_block(rw, torch, dev, flush, stream, steps=100, quick=False):
-    """The 128^3 volume (6-connected, 2 labels, 500 seeds per label, m = 100): precompute,
-    online solves (adaptive m, 3 refinement steps), and the equal-accuracy comparison (skipped
-    when quick: timing and phases only, for profiling runs)."""
+def c3_block(rw, torch, dev, flush, stream, steps=100, quick=False, hbm=HBM_FALLBACK):
+    """The 128^3 volume (6-connected, 2 labels, 500 seeds per label): precompute m = 100
+    eigenvectors, then online solves at the configuration's fixed m = 100 (the 128^3 line) and,
+    beside it, with m chosen adaptively; 3 refinement steps; the equal-accuracy comparison at
+    m = 100 (skipped when quick: timing and phases only, for profiling runs)."""
     J, dims, truth = synth.ellipsoid_volume(128, seed=synth.BASE_SEED + 2)
     N = int(np.prod(dims))
     g = rw.rw_build_graph(torch.from_numpy(J.astype(np.float32)).to(dev), dims, BETA)
@@ -308,20 +350,27 @@ def c3_block(rw, torch, dev, flush, stream, steps=100, quick=False):
     dp = [(torch.from_numpy(si).to(dev), torch.from_numpy(sl).to(dev)) for si, sl in pool]
     prob = torch.empty(N, 2, device=dev)
     lab = torch.empty(N, dtype=torch.uint8, device=dev)
-    kw = dict(gamma=GAMMA, m=0, m_step=M_STEP, eps=EPS, refine_steps=REFINE)
-    for k in range(3):
-        rw.rw_solve(g, b, dp[k][0], dp[k][1], 2, prob, lab, want_info=False, **kw)
-    ms = time_steps(lambda k: rw.rw_solve(g, b, dp[k % 20][0], dp[k % 20][1], 2, prob, lab,
-                                          want_info=False, **kw), steps, flush, stream)
-    infos = [rw.rw_solve(g, b, dp[k % 20][0], dp[k % 20][1], 2, prob, lab, record_phases=True,
-                         **kw)[1] for k in range(40)]
-    phases = {p: float(np.mean([i["phase_ms"][p] for i in infos])) for p in rw.RW_PHASES}
+    out = {"workload": "rwis-128x128x128-2label-ellipsoid", "m": 100,
+           "l2": "flushed (256 MB write) before every timed step"}
+    for tag, m in (("fixed_m100", 100), ("adaptive", 0)):
+        kw = dict(gamma=GAMMA, m=m, m_step=M_STEP, eps=EPS, refine_steps=REFINE)
+        for k in range(3):
+            rw.rw_solve(g, b, dp[k][0], dp[k][1], 2, prob, lab, want_info=False, **kw)
+        ms = time_steps(lambda k: rw.rw_solve(g, b, dp[k % 20][0], dp[k % 20][1], 2, prob, lab,
+                                              want_info=False, **kw), steps, flush, stream)
+        infos = [rw.rw_solve(g, b, dp[k % 20][0], dp[k % 20][1], 2, prob, lab,
+                             record_phases=True, **kw)[1] for k in range(40)]
+        phases = {p: float(np.mean([i["phase_ms"][p] for i in infos])) for p in rw.RW_PHASES}
+        out[tag] = {"label_maps_per_s": 1000.0 / ms, "ms_per_step": ms, "steps": steps,
+                    "m_used_mean": float(np.mean([i["m_used"] for i in infos])),
+                    "phase_ms": phases}
+    out["label_maps_per_s"] = out["fixed_m100"]["label_maps_per_s"]
     if quick:
         rw.rw_basis_free(b)
         rw.rw_graph_free(g)
-        return {"workload": "rwis-128x128x128-2label-ellipsoid", "label_maps_per_s": 1000.0 / ms,
-                "ms_per_step": ms, "steps": steps, "phase_ms": phases,
-                "partial": "profiling run (--c3-only)"}
+        out["partial"] = "profiling run (--c3-only)"
+        return out
+    kw = dict(gamma=GAMMA, m=100, m_step=M_STEP, eps=EPS, refine_steps=REFINE)
     si0, sl0 = dp[0]
     conv = torch.empty(N, 2, device=dev)
     tmp = torch.empty(N, 2, device=dev)
@@ -335,18 +384,111 @@ def c3_block(rw, torch, dev, flush, stream, steps=100, quick=False):
                                                   gamma=GAMMA, iters=pcg_iters,
                                                   want_iters=False), 10, flush, stream)
     rw.rw_solve(g, b, si0, sl0, 2, prob, lab, want_info=False, **kw)
-    fast_vs_exact = float((prob - conv).abs().max())
-    equal = equal_accuracy(rw, g, b, dp, conv, tmp, lab, flush, stream, kw, pcg_ms, pcg_iters,
-                           n_labels=2)
+    out["fast_vs_exact_maxabs"] = float((prob - conv).abs().max())
+    rw.rw_solve(g, b, si0, sl0, 2, prob, lab, want_info=False, **{**kw, "m": 0})
+    out["adaptive"]["fast_vs_exact_maxabs"] = float((prob - conv).abs().max())
+    out["pcg_competitor"] = {"iters_to_1e-3": pcg_iters, "iters_converged_1e-7": it_conv,
+                             "ms_per_step": pcg_ms, "label_maps_per_s": 1000.0 / pcg_ms,
+                             "per_iteration_us": 1000.0 * pcg_ms / pcg_iters,
+                             "roofline": pcg_roofline(N, 4, 3, pcg_ms / pcg_iters, hbm)}
+    out["equal_accuracy"] = equal_accuracy(rw, g, b, dp, conv, tmp, lab, flush, stream, kw,
+                                           pcg_ms, pcg_iters, n_labels=2)
+    out["precompute"] = {"seconds": pre_s, **info}
     rw.rw_basis_free(b)
     rw.rw_graph_free(g)
-    return {"workload": "rwis-128x128x128-2label-ellipsoid", "label_maps_per_s": 1000.0 / ms,
-            "ms_per_step": ms, "steps": steps, "m_used_mean": float(np.mean([i["m_used"] for i in infos])),
-            "phase_ms": phases, "fast_vs_exact_maxabs": fast_vs_exact,
-            "pcg_competitor": {"iters_to_1e-3": pcg_iters, "iters_converged_1e-7": it_conv,
-                               "ms_per_step": pcg_ms, "label_maps_per_s": 1000.0 / pcg_ms},
-            "equal_accuracy": equal, "precompute": {"seconds": pre_s, **info},
-            "l2": "flushed (256 MB write) before every timed step"}
+    return out
+
+
+def stencil_block(rw, torch, dev, cases):
+    """Matrix-free Y = L-hat X (Sec. II-C, Eq. z_eig) on N x k blocks: CUDA-event time per
+    apply and achieved algorithmic bandwidth.  The blocks (210 MB at 512^2 x 200, 839 MB at
+    128^3 x 100) exceed the 129 MB L2, so nothing is flushed in between."""
+    out = {}
+    for name, g, dims, k in cases:
+        N = int(np.prod(dims))
+        gen = torch.Generator(device=dev)
+        gen.manual_seed(5)
+        X = torch.randn(N, k, device=dev, generator=gen)
+        Y = torch.empty(N, k, device=dev)
+        for _ in range(3):
+            rw.rw_apply_laplacian(g, X, Y, k)
+        reps = 20
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(reps)]
+        st = torch.cuda.current_stream()
+        for a, z in ev:
+            a.record(st)
+            rw.rw_apply_laplacian(g, X, Y, k)
+            z.record(st)
+        torch.cuda.synchronize()
+        ms = float(np.mean([a.elapsed_time(z) for a, z in ev]))
+        byts = N * stencil_bytes_per_node(k, len(dims))
+        out[name] = {"k": k, "ms_per_apply": ms, "algorithmic_bytes": byts,
+                     "achieved_gbs": byts / (ms * 1e-3) / 1e9}
+        del X, Y
+    return out
+
+
+def beta_update_block(rw, torch, dev, g, b, J32, dims, truth, flush, stream, n_sets=4):
+    """Sec. III-B on the 512^2 workload: the basis precomputed at beta = 90 is updated to
+    beta = 150 by the Rayleigh-quotient values of Eq. (z_ray) (eigenvectors kept), and compared
+    with a basis recomputed from scratch at beta = 150; both solve the same seed sets
+    (adaptive m, 3 refinement steps) and are compared with the converged basic RW at
+    beta = 150.  Mutates g and b (run last)."""
+    N = int(np.prod(dims))
+    sets = seed_sets(truth, dims, n_sets, synth.BASE_SEED + 9001)
+    dsets = [(torch.from_numpy(si).to(dev), torch.from_numpy(sl).to(dev)) for si, sl in sets]
+    kw = dict(gamma=GAMMA, m=0, m_step=M_STEP, eps=EPS, refine_steps=REFINE)
+    prob = torch.empty(N, LABELS, device=dev)
+    lab = torch.empty(N, dtype=torch.uint8, device=dev)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ev0.record(stream)
+    rw.rw_update_weights(g, b, rw.RW_UPDATE_BETA, beta=BETA_NEW)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    upd_wall = time.perf_counter() - t0
+    upd_ms = ev0.elapsed_time(ev1)
+    g2 = rw.rw_build_graph(J32, dims, BETA_NEW)
+    t0 = time.perf_counter()
+    b2, info2 = rw.rw_precompute(g2, M, tol=1e-5, seed=1)
+    torch.cuda.synchronize()
+    re_s = time.perf_counter() - t0
+    conv = torch.empty(N, LABELS, device=dev)
+    rows = {"updated": [], "recomputed": []}
+    lab_ex = torch.empty(N, dtype=torch.uint8, device=dev)
+    for si, sl in dsets:
+        rw.rw_solve_pcg(g2, si, sl, LABELS, conv, lab_ex, gamma=GAMMA, iters=50000, tol=1e-7)
+        for tag, gg, bb in (("updated", g, b), ("recomputed", g2, b2)):
+            _, inf = rw.rw_solve(gg, bb, si, sl, LABELS, prob, lab, **kw)
+            rows[tag].append({"maxabs": float((prob - conv).abs().max()),
+                              "label_agreement": float((lab == lab_ex).float().mean()),
+                              "m_used": inf["m_used"]})
+    lam_upd = rw.rw_basis_get(b)
+    lam_re = rw.rw_basis_get(b2)
+    ms = {}
+    for tag, gg, bb in (("updated", g, b), ("recomputed", g2, b2)):
+        ms[tag] = time_steps(lambda k: rw.rw_solve(gg, bb, dsets[k % n_sets][0],
+                                                   dsets[k % n_sets][1], LABELS, prob, lab,
+                                                   want_info=False, **kw), 20, flush, stream)
+    rw.rw_basis_free(b2)
+    rw.rw_graph_free(g2)
+
+    def summary(tag):
+        r = rows[tag]
+        return {"maxabs_vs_exact_mean": float(np.mean([x["maxabs"] for x in r])),
+                "maxabs_vs_exact_max": float(np.max([x["maxabs"] for x in r])),
+                "label_agreement_mean": float(np.mean([x["label_agreement"] for x in r])),
+                "m_used_mean": float(np.mean([x["m_used"] for x in r])),
+                "solve_ms": ms[tag]}
+    return {"beta_from": BETA, "beta_to": BETA_NEW, "seed_sets": n_sets,
+            "update_ms": upd_ms, "update_wall_s": upd_wall, "recompute_s": re_s,
+            "recompute_info": info2,
+            "values_rel_diff_median": float(np.median(np.abs(lam_upd - lam_re)
+                                                      / np.maximum(np.abs(lam_re), 1e-3))),
+            "updated": summary("updated"), "recomputed": summary("recomputed"),
+            "reference": "basic RW at beta = 150 by PCG to a relative residual of 1e-7"}
 
 
 def max_over_ranks(ms, world, device=None):
@@ -381,6 +523,35 @@ def gpu_arm(args):
         with open(pk) as f:
             peaks = json.load(f)
 
+    if args.stencil_only or args.pcg_only:  # profiling runs of one kernel
+        out = {}
+        J2, dims2, truth2 = synth.voronoi_image(SIZE, SIZE, seed=synth.BASE_SEED + 1)
+        J3, dims3, truth3 = synth.ellipsoid_volume(128, seed=synth.BASE_SEED + 2)
+        g2 = rw.rw_build_graph(torch.from_numpy(J2.astype(np.float32)).to(dev), dims2, BETA)
+        g3 = rw.rw_build_graph(torch.from_numpy(J3.astype(np.float32)).to(dev), dims3, BETA)
+        hbm = peaks.get("hbm_gbs") or HBM_FALLBACK
+        if args.stencil_only:
+            out["stencil"] = stencil_block(rw, torch, dev, [("512x512_k200", g2, dims2, 200),
+                                                            ("128x128x128_k100", g3, dims3, 100)])
+        if args.pcg_only:
+            for name, g_, dims_, truth_, per, L in (("512x512", g2, dims2, truth2, 200, 4),
+                                                    ("128x128x128", g3, dims3, truth3, 500, 2)):
+                si, sl = synth.sample_seeds(truth_, dims_, per, 2, seed=synth.BASE_SEED + 31)
+                si, sl = torch.from_numpy(si).to(dev), torch.from_numpy(sl).to(dev)
+                N_ = int(np.prod(dims_))
+                pr = torch.empty(N_, L, device=dev)
+                it = 100
+                ms_ = time_steps(lambda k: rw.rw_solve_pcg(g_, si, sl, L, pr, gamma=GAMMA,
+                                                           iters=it, want_iters=False),
+                                 5, torch.empty(L2_FLUSH_BYTES // 4, device=dev),
+                                 torch.cuda.current_stream())
+                out["pcg_" + name] = {"iters": it, "ms": ms_, "per_iteration_us": 1000 * ms_ / it,
+                                      "roofline": pcg_roofline(N_, 4, len(dims_), ms_ / it, hbm)}
+        rw.rw_graph_free(g2)
+        rw.rw_graph_free(g3)
+        if rank == 0:
+            print(json.dumps(out))
+        return 0
     if args.c3_only:  # profiling runs of the 128^3 workload
         flush = torch.empty(L2_FLUSH_BYTES // 4, device=dev)
         out = c3_block(rw, torch, dev, flush, torch.cuda.current_stream(), steps=args.steps,
@@ -519,15 +690,42 @@ def gpu_arm(args):
     fast_vs_exact = float((prob - conv).abs().max())
     equal = equal_accuracy(rw, g, b, dsets[args.warmup:], conv, tmp, labels, flush, stream,
                            kw, pcg_ms, pcg_iters)
-    c3 = None if args.no_c3 else c3_block(rw, torch, dev, flush, stream)
+    c3 = None if args.no_c3 else c3_block(rw, torch, dev, flush, stream, hbm=hbm)
+    stencil = None
+    if not args.no_stencil:
+        cases = [("512x512_k200", g, dims, 200)]
+        if not args.no_c3:
+            J3, dims3, _ = synth.ellipsoid_volume(128, seed=synth.BASE_SEED + 2)
+            g3 = rw.rw_build_graph(torch.from_numpy(J3.astype(np.float32)).to(dev), dims3, BETA)
+            cases.append(("128x128x128_k100", g3, dims3, 100))
+        stencil = stencil_block(rw, torch, dev, cases)
+        for v in stencil.values():
+            v["peak"] = hbm
+            v["frac"] = v["achieved_gbs"] / hbm
+        if not args.no_c3:
+            rw.rw_graph_free(g3)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        times = time_oracle(20, budget_s=25.0)
+        # the FP64 oracle's online solve on the GPU's own basis (copied to the host once,
+        # untimed), adaptive m on the same seed sets as the phase pass: the same arithmetic
+        Qd = torch.empty(N, M, device=dev)
+        lam_gpu = rw.rw_basis_get(b, Qd)
+        Qh = Qd.cpu().numpy().astype(np.float64)
+        del Qd
+        osets = [(si.cpu().numpy(), sl.cpu().numpy()) for si, sl in dsets[args.warmup:args.warmup + 20]]
+        times, m_or = time_oracle_on(J, dims, Qh, lam_gpu, osets, budget_s=25.0)
+        agree = int(sum(int(a == b_) for a, b_ in zip(m_or, m_used)))
         cpu = {"value": 1000.0 / (1000.0 * float(np.mean(times))), "unit": "label_maps/s",
                "cores": cpu_cores(), "kind": "oracle",
-               "sample": f"{len(times)} full 512x512 online solves of the FP64 oracle (DCT basis "
-                         f"of the same shape; adaptive m, 3 refinement steps)"}
+               "sample": f"{len(times)} full 512x512 online solves of the FP64 oracle on the "
+                         f"GPU's own LOBPCG basis (m <= 200, adaptive m, 3 refinement steps), "
+                         f"same seed sets as the GPU phase pass",
+               "same_config": True,
+               "adaptive_m_agreement": f"{agree}/{len(m_or)}"}
+    beta_upd = None if args.no_beta_update else beta_update_block(
+        rw, torch, dev, g, b, J32, dims, truth, flush, stream)
+    pcg_roof = pcg_roofline(N, 4, 2, pcg_ms / pcg_iters, hbm)
 
     line = {
         "metric": METRIC, "value": value, "unit": "label_maps/s", "n_gpus": world,
@@ -548,12 +746,16 @@ def gpu_arm(args):
         "gpu_launches": int(launches),
         "clocks": clocks,
         "pcg_competitor": {"iters_to_1e-3": pcg_iters, "iters_converged_1e-7": it_conv,
-                           "ms_per_step": pcg_ms, "label_maps_per_s": 1000.0 / pcg_ms},
+                           "ms_per_step": pcg_ms, "label_maps_per_s": 1000.0 / pcg_ms,
+                           "per_iteration_us": 1000.0 * pcg_ms / pcg_iters,
+                           "roofline": pcg_roof},
         "fast_vs_exact_maxabs": fast_vs_exact,
         "equal_accuracy": equal,
         "phases": phase_roofs,
         "precompute": {"seconds": precompute_s, **eig_info},
         "c3_128cubed": c3,
+        "stencil": stencil,
+        "beta_update_512": beta_upd,
     }
     rw.rw_basis_free(b)
     rw.rw_graph_free(g)
@@ -574,6 +776,13 @@ def main():
     ap.add_argument("--no-competitor", action="store_true",
                     help="skip the e2e, PCG and CPU legs (profiling runs)")
     ap.add_argument("--no-c3", action="store_true", help="skip the 128^3 block")
+    ap.add_argument("--no-stencil", action="store_true", help="skip the stencil block")
+    ap.add_argument("--stencil-only", action="store_true",
+                    help="only time the Laplacian stencil (profiling runs)")
+    ap.add_argument("--pcg-only", action="store_true",
+                    help="only time 100 PCG iterations at 512^2 and 128^3 (profiling runs)")
+    ap.add_argument("--no-beta-update", action="store_true",
+                    help="skip the beta 90 -> 150 update-vs-recompute block")
     ap.add_argument("--c3-only", action="store_true",
                     help="only time the 128^3 workload (profiling runs)")
     args = ap.parse_args()
