@@ -41,12 +41,29 @@ def mask_loss(U, truth, seed_idx, label=1):
     return float(diff @ diff), G
 
 
-def exact_grad(g, seed_idx, seed_lab, n_labels, P, gamma, dloss_dU, normalized=True, U=None):
-    """Returns (dloss/dw over g.ids order, dloss/dbeta)."""
+def exact_grad(g, seed_idx, seed_lab, n_labels, P, gamma, dloss_dU, normalized=True, U=None,
+               method="splu", tol=1e-12):
+    """Returns (dloss/dw over g.ids order, dloss/dbeta).  The forward and the adjoint system are
+    solved by SuperLU (``method="splu"``) or, for graphs too large to factor (3-D volumes), by
+    FP64 conjugate gradients to ||r|| <= tol ||b|| per column (``method="cg"``)."""
     if U is None:
-        U = exact_rw(g, seed_idx, seed_lab, n_labels, P, gamma, normalized)
+        U = exact_rw(g, seed_idx, seed_lab, n_labels, P, gamma, normalized, method=method,
+                     tol=tol)
     A, _, n = system(g, seed_idx, seed_lab, n_labels, P, gamma, normalized)
-    lam_n = spla.splu(A.tocsc()).solve(np.asarray(dloss_dU[n]))
+    G = np.asarray(dloss_dU[n])
+    if method == "splu":
+        lam_n = spla.splu(A.tocsc()).solve(G)
+    elif method == "cg":
+        lam_n = np.zeros_like(G)
+        for k in range(G.shape[1]):
+            if not np.any(G[:, k]):
+                continue
+            x, info = spla.cg(A, G[:, k], rtol=tol, atol=0.0, maxiter=200000)
+            if info != 0:
+                raise RuntimeError("CG did not converge")
+            lam_n[:, k] = x
+    else:
+        raise ValueError(method)
     lam = np.zeros_like(U)
     lam[n] = lam_n
     a, b = g.a, g.b
