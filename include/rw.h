@@ -97,6 +97,21 @@ rw_status rw_graph_weights(const rw_graph* g, float* w_dev, float* d_dev, void* 
 rw_status rw_apply_laplacian(const rw_graph* g, const float* X_dev, int64_t ldx, float* Y_dev,
                              int64_t ldy, int32_t k, void* stream);
 
+/* Gram product G = A^T B of two tall node-major FP32 blocks on the tensor cores, the dense
+ * contraction of the eigensolver's Rayleigh-Ritz and orthogonalization steps (Sec. II-B,
+ * Eq. L_eigs: the projected matrices of the block).  A_dev: N x p (pitch lda), B_dev: N x q
+ * (pitch ldb); G_dev: p x q FP64 row-major (pitch ldg >= q), overwritten.  Products are taken
+ * as three TF32 products of a hi/lo split of each FP32 value (about 21 bits per product), summed
+ * in FP32 over slices of 1024 rows and in FP64, in a fixed order, over the slices.
+ * scratch_dev (caller-owned, 256-byte aligned) holds at least
+ * rw_block_gram_scratch_bytes(N, p, q) bytes; its first int is a device status word (bit
+ * RW_DEV_TIMEOUT = 64 set if a bounded wait of the tensor-core pipeline gave up; cleared by
+ * every call).  1 <= p, q; N >= 0; N <= 67,107,840.  Asynchronous on `stream`. */
+size_t rw_block_gram_scratch_bytes(int64_t N, int32_t p, int32_t q);
+rw_status rw_block_gram(const float* A_dev, int64_t lda, const float* B_dev, int64_t ldb,
+                        int64_t N, int32_t p, int32_t q, double* G_dev, int32_t ldg,
+                        void* scratch_dev, size_t scratch_bytes, void* stream);
+
 /* ------------------------------------------------------------------------------------------
  * Offline precomputation (Sec. II-B, Eq. L_eigs): the m smallest eigenpairs of L-hat (or L).
  * The paper names no eigensolver; this is a block LOBPCG (blocks [X, W, P], soft locking)
@@ -130,6 +145,19 @@ rw_status rw_precompute(rw_graph* g, const rw_eig_opts* opts, void* stream, rw_b
  * both; builds the 16-bit copy used by the online solve. */
 rw_status rw_basis_create(const rw_graph* g, int32_t m, const float* Q_dev,
                           const double* lambda_host, void* stream, rw_basis** out);
+/* Saving and loading a basis (the paper's discussion of memory, Sec. V: precomputed
+ * eigenvectors are stored offline and loaded as needed, possibly only the leading ones).
+ * rw_basis_save writes the basis's current values and its FP32 columns, with the graph's dims,
+ * beta and form, to `path` (overwritten; 64-byte header, then m doubles, then N x m floats,
+ * host byte order).  rw_basis_load creates a basis for g from such a file, keeping only the
+ * first m_load columns (0 = all; the file is read a block of rows at a time, so host memory
+ * stays small); the file must belong to a graph of g's dims and form (RW_ERR_INVALID_ARG with a
+ * message otherwise, and for a missing, foreign or truncated file).  Both synchronize; the
+ * loaded basis is owned by the caller (rw_basis_free). */
+rw_status rw_basis_save(const rw_basis* b, const char* path, void* stream);
+rw_status rw_basis_load(const rw_graph* g, const char* path, int32_t m_load, void* stream,
+                        rw_basis** out);
+
 /* Copies Q (N x m, ld = m, FP32) and/or the current values (m doubles) out.  Synchronizes. */
 rw_status rw_basis_get(const rw_basis* b, float* Q_dev, double* lambda_host, void* stream);
 int32_t rw_basis_m(const rw_basis* b);

@@ -285,3 +285,31 @@ def rw_rayleigh_quotients_noalloc(g, Q, lam_out, m=None, stream=None):
     return _check(abi.lib().rw_rayleigh_quotients_noalloc(g, _dp(Q), _ld(Q), m, _dp(lam_out),
                                                           _stream(stream)),
                   "rw_rayleigh_quotients_noalloc")
+
+
+def rw_block_gram_scratch_bytes(N, p, q):
+    return abi.lib().rw_block_gram_scratch_bytes(N, p, q)
+
+
+def rw_block_gram(A, B, G, scratch, stream=None):
+    """G (p x q float64, CUDA) = A^T B for CUDA float32 blocks A (N x p), B (N x q) on the
+    tensor cores; scratch: a CUDA byte tensor of rw_block_gram_scratch_bytes(N, p, q)."""
+    N, p = A.shape
+    q = B.shape[1]
+    if B.shape[0] != N or G.shape[0] < p or G.shape[1] < q:
+        raise ValueError("shapes: A N x p, B N x q, G at least p x q")
+    return _check(abi.lib().rw_block_gram(_dp(A), _ld(A), _dp(B), _ld(B), N, p, q, _dp(G),
+                                          _ld(G), _dp(scratch), scratch.numel() * scratch.element_size(),
+                                          _stream(stream)), "rw_block_gram")
+
+
+def rw_basis_save(b, path, stream=None):
+    return _check(abi.lib().rw_basis_save(b, str(path).encode(), _stream(stream)),
+                  "rw_basis_save")
+
+
+def rw_basis_load(g, path, m_load=0, stream=None):
+    h = C.c_void_p()
+    _check(abi.lib().rw_basis_load(g, str(path).encode(), m_load, _stream(stream), C.byref(h)),
+           "rw_basis_load")
+    return h.value

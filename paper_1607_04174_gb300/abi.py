@@ -107,6 +107,10 @@ PROTOTYPES = {
     "rw_grad_fast": (I32, [P, P, P, P, I32, I32, P, D, I32, I32, D, P, P, P, C.POINTER(D), P]),
     "rw_solve_priors": (I32, [P, P, P, I32, I32, P, P]),
     "rw_rayleigh_quotients_noalloc": (I32, [P, P, I64, I32, P, P]),
+    "rw_block_gram_scratch_bytes": (C.c_size_t, [I64, I32, I32]),
+    "rw_basis_save": (I32, [P, C.c_char_p, P]),
+    "rw_basis_load": (I32, [P, C.c_char_p, I32, P, HP]),
+    "rw_block_gram": (I32, [P, I64, P, I64, I64, I32, I32, P, I32, P, C.c_size_t, P]),
 }
 
 _lib = None

@@ -123,7 +123,7 @@ struct Work {
   cudaStream_t st;
   const rw_graph* g;
   int64_t N;
-  DevBuf S, AS, T, Pb, small;
+  DevBuf S, AS, T, Pb, small, gsc;   // gsc: scratch of the tensor-core Gram
   int ldS;
   double *H, *V, *w, *eigw, *G, *cn;
   float *C32, *Rinv, *lam32;
@@ -135,9 +135,12 @@ bool trace_on();
 void trace_block(Work& W, const char* what, const float* A, int64_t lda, int k);
 void trace_small(Work& W, const char* what, const double* M, int n);
 
+// Gram of two N-row blocks: tensor cores (rw_gram_tc) for the eigensolver's projected
+// matrices; its scratch grows once to the largest shape met
 rw_status gram_into(Work& W, const float* A, int64_t lda, const float* B, int64_t ldb, int p,
                     int q, double* G) {
-  return rw_gram(A, lda, B, ldb, W.N, p, q, G, q, false, W.st);
+  RW_TRY(W.gsc.grow(rw_gram_tc_scratch_bytes(W.N, p, q)));
+  return rw_gram_tc(A, lda, B, ldb, W.N, p, q, G, q, false, W.gsc.p, W.g->status, W.st);
 }
 
 rw_status colnorms(Work& W, const float* A, int64_t lda, int k, std::vector<double>& out);
@@ -283,7 +286,7 @@ rw_status colnorms(Work& W, const float* A, int64_t lda, int k, std::vector<doub
 // coefficients of the first k Ritz vectors -> C32 (n x k), rows < zero_rows zeroed.
 rw_status rayleigh_ritz(Work& W, const float* S, const float* AS, int n, int k,
                         std::vector<double>& w_h) {
-  RW_TRY(rw_gram(S, W.ldS, AS, W.ldS, W.N, n, n, W.H, n, false, W.st));
+  RW_TRY(gram_into(W, S, W.ldS, AS, W.ldS, n, n, W.H));
   k_symmetrize<<<rw_blocks((int64_t)n * n, 256), 256, 0, W.st>>>(W.H, n);
   RW_LAUNCH_CHECK();
   trace_small(W, "rr H", W.H, n);
@@ -395,7 +398,10 @@ extern "C" rw_status rw_precompute(rw_graph* g, const rw_eig_opts* opts, void* s
   const size_t blk = sizeof(float) * (size_t)g->N * W.ldS;
   struct Guard {
     Work& w;
-    ~Guard() { w.S.release(); w.AS.release(); w.T.release(); w.Pb.release(); w.small.release(); }
+    ~Guard() {
+      w.S.release(); w.AS.release(); w.T.release(); w.Pb.release(); w.small.release();
+      w.gsc.release();
+    }
   } guard_rel{W};
   RW_TRY(W.S.grow(blk));
   RW_TRY(W.AS.grow(blk));
@@ -589,6 +595,7 @@ extern "C" rw_status rw_precompute(rw_graph* g, const rw_eig_opts* opts, void* s
     // stored values: edge-sum Rayleigh quotients (Eq. z_ray) of the stored FP32 columns, so a
     // later update with unchanged weights reproduces them exactly
     rw_status rs = rw_basis_rayleigh(g, b, W.st);
+    if (rs == RW_OK) rs = rw_last_device_status(g, W.st);  // e.g. a tensor-core wait gave up
     if (rs != RW_OK) { rw_basis_free(b); return rs; }
     *out = b;
   }

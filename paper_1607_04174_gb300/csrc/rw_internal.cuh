@@ -177,6 +177,13 @@ rw_status rw_set_all_weights(rw_graph* g, const float* w_dev, cudaStream_t st);
 // G (p x q, row-major, ldg, FP64) = (accumulate ? G : 0) + A^T B, A: N x p (lda), B: N x q (ldb)
 rw_status rw_gram(const float* A, int64_t lda, const float* B, int64_t ldb, int64_t N, int p,
                   int q, double* G, int ldg, bool accumulate, cudaStream_t st);
+// gram_tc.cu: the same G = (accumulate ? G : 0) + A^T B on the tensor cores (TF32 x 3 split,
+// FP32 over 1024-row slices, FP64 over slices); scratch of rw_gram_tc_scratch_bytes(N, p, q)
+// bytes, 256-byte aligned; status: device status word (RW_DEV_TIMEOUT on a failed wait)
+size_t rw_gram_tc_scratch_bytes(int64_t N, int p, int q);
+rw_status rw_gram_tc(const float* A, int64_t lda, const float* B, int64_t ldb, int64_t N, int p,
+                     int q, double* G, int ldg, bool accumulate, void* scratch, int* status,
+                     cudaStream_t st);
 // Y (N x p) = alpha * A (N x q) * C (q x p, row-major FP32, ldc) + beta * Y
 rw_status rw_gemm_tall(const float* A, int64_t lda, const float* C, int ldc, int64_t N, int q,
                        int p, float alpha, float beta, float* Y, int64_t ldy, cudaStream_t st);
@@ -203,6 +210,10 @@ rw_status rw_solve_priors_internal(const rw_graph* g, const int32_t* seed_idx,
                                    bool defer_priors = false);
 rw_status launch_priors(const rw_graph* g, int L, int prior_mode, const float* priors, int lp,
                         int early, cudaStream_t st);
+
+// eig.cu: a basis handle from N x m columns X (pitch ldx, device) and m host values (syncs)
+rw_status rw_make_basis(const rw_graph* g, int m, const float* X, int64_t ldx,
+                        const double* lam_h, cudaStream_t st, rw_basis** out);
 
 // update.cu: edge-sum Rayleigh quotients of every basis column under g -> b->lam (synchronizes)
 rw_status rw_basis_rayleigh(const rw_graph* g, rw_basis* b, cudaStream_t st);

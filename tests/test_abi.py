@@ -86,7 +86,7 @@ def _null_args(argtypes):
     """Integers 1, doubles 1.0, every pointer NULL."""
     args = []
     for t in argtypes:
-        if t in (C.c_int32, C.c_int64):
+        if t in (C.c_int32, C.c_int64, C.c_size_t):
             args.append(1)
         elif t is C.c_double:
             args.append(1.0)
@@ -109,11 +109,14 @@ def test_null_handles_are_refused_on_the_host(lib):
         assert st == -1, (name, st)
     assert lib.rw_basis_m(None) == 0
     assert lib.rw_graph_num_nodes(None) == 0
+    assert lib.rw_block_gram_scratch_bytes(1, 0, 1) == 0
+    assert lib.rw_block_gram_scratch_bytes(2048, 128, 256) == 256 + 4 * 128 * 256 * 2
     lib.rw_graph_free(None)
     lib.rw_basis_free(None)
     assert lib.rw_kernel_launches() == before
     # every declared entry point is one of the calls above or an accessor checked elsewhere
     covered = set(status_calls) | {"rw_basis_m", "rw_graph_num_nodes", "rw_graph_free",
+                                   "rw_block_gram_scratch_bytes",
                                    "rw_basis_free", "rw_status_str", "rw_last_error_message",
                                    "rw_kernel_launches"}
     assert set(_declared()) <= covered, sorted(set(_declared()) - covered)

@@ -22,11 +22,18 @@ def _strip_comments(text):
 
 
 def test_mbarrier_waits_are_bounded():
-    """The only mbarrier poll is mbar_try_wait, and its only caller is the bounded loop that
-    gives up (setting a timeout status) after a fixed number of polls."""
+    """The mbarrier polls are mbar_try_wait (solve.cu) and mbar_poll (gram_tc.cu); each has one
+    caller, a bounded loop that gives up (setting a timeout status) after a fixed number of
+    polls."""
     src = {f: _strip_comments(t) for f, t in _sources().items()}
     polls = [f for f, t in src.items() for _ in re.finditer(r"mbarrier\.try_wait", t)]
-    assert polls == ["solve.cu"]
+    assert sorted(polls) == ["gram_tc.cu", "solve.cu"]
+    g = src["gram_tc.cu"]
+    assert len(re.findall(r"\bmbar_poll\s*\(", g)) == 2
+    i = g.index("bool mbar_wait_limited(")
+    body = g[i:g.index("\n}\n", i)]
+    assert "mbar_poll(" in body and "RW_DEV_TIMEOUT" in body and "return false;" in body
+    assert re.search(r"it\s*<=\s*\(1\s*<<\s*\d+\)", body)
     uses = re.findall(r"\bmbar_try_wait\s*\(", src["solve.cu"])
     assert len(uses) == 2  # its definition and the call inside mbar_wait_bounded
     i = src["solve.cu"].index("void mbar_wait_bounded(")
