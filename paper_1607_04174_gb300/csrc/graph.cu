@@ -2,6 +2,8 @@
 // (Sec. II-C) and the matrix-free Laplacian apply on node-major N x k blocks.
 #include "rw_internal.cuh"
 
+#include <algorithm>
+
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -211,6 +213,57 @@ k_stencil_wide(const float* __restrict__ X, int64_t ldx, float* __restrict__ Y, 
   }
 }
 
+// Grid graphs, the bandwidth-bound default: one thread per (voxel, float4 chunk of its row).
+// Threads of a row of voxels are consecutive (chunk fastest), so a warp reads 512 contiguous
+// bytes of X per access and every thread issues its own row and all 2 ndim neighbour rows at
+// once (the x neighbours hit L1, the y and z neighbours L2).  y and z come from the block
+// index; one division by the chunk count per thread.
+__global__ void __launch_bounds__(256)
+k_stencil_flat(const float* __restrict__ X, int64_t ldx, float* __restrict__ Y, int64_t ldy,
+               int nch, const float* __restrict__ cw, const float* __restrict__ dg,
+               int normalized, int ndim, int DX, int DY, int DZ, int64_t N, float alpha,
+               float beta, const float* __restrict__ Zm, int64_t ldz, float gamma) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= DX * nch) return;
+  const int x = t / nch, c = t - x * nch;
+  const int y = blockIdx.y, z = blockIdx.z;
+  const int64_t sy = DX, sz = (int64_t)DX * DY;
+  const int64_t i = x + sy * y + sz * z;
+  auto ld = [&](int64_t j) { return __ldg(reinterpret_cast<const float4*>(X + j * ldx) + c); };
+  const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+  // every load first: own row, the neighbours, their coefficients
+  const float4 xo = ld(i);
+  const bool hx0 = x > 0, hx1 = x + 1 < DX, hy0 = y > 0, hy1 = y + 1 < DY;
+  const bool hz0 = ndim == 3 && z > 0, hz1 = ndim == 3 && z + 1 < DZ;
+  const float4 vx0 = hx0 ? ld(i - 1) : zero, vx1 = hx1 ? ld(i + 1) : zero;
+  const float4 vy0 = hy0 ? ld(i - sy) : zero, vy1 = hy1 ? ld(i + sy) : zero;
+  const float4 vz0 = hz0 ? ld(i - sz) : zero, vz1 = hz1 ? ld(i + sz) : zero;
+  const float cx0 = hx0 ? __ldg(cw + i - 1) : 0.f, cx1 = hx1 ? __ldg(cw + i) : 0.f;
+  const float cy0 = hy0 ? __ldg(cw + N + i - sy) : 0.f, cy1 = hy1 ? __ldg(cw + N + i) : 0.f;
+  const float cz0 = hz0 ? __ldg(cw + 2 * N + i - sz) : 0.f;
+  const float cz1 = hz1 ? __ldg(cw + 2 * N + i) : 0.f;
+  const float dd = normalized ? 1.f : __ldg(dg + i);
+  float4 zz = zero;
+  if (Zm) zz = __ldg(reinterpret_cast<const float4*>(Zm + i * ldz) + c);
+  auto lap = [&](float o, float a0, float a1, float b0, float b1, float e0, float e1) {
+    float acc = dd * o;
+    acc = fmaf(-cx0, a0, acc); acc = fmaf(-cx1, a1, acc);
+    acc = fmaf(-cy0, b0, acc); acc = fmaf(-cy1, b1, acc);
+    acc = fmaf(-cz0, e0, acc); acc = fmaf(-cz1, e1, acc);
+    return alpha * acc + beta * o;
+  };
+  float4 out;
+  out.x = lap(xo.x, vx0.x, vx1.x, vy0.x, vy1.x, vz0.x, vz1.x);
+  out.y = lap(xo.y, vx0.y, vx1.y, vy0.y, vy1.y, vz0.y, vz1.y);
+  out.z = lap(xo.z, vx0.z, vx1.z, vy0.z, vy1.z, vz0.z, vz1.z);
+  out.w = lap(xo.w, vx0.w, vx1.w, vy0.w, vy1.w, vz0.w, vz1.w);
+  if (Zm) {
+    out.x = fmaf(gamma, zz.x, out.x); out.y = fmaf(gamma, zz.y, out.y);
+    out.z = fmaf(gamma, zz.z, out.z); out.w = fmaf(gamma, zz.w, out.w);
+  }
+  reinterpret_cast<float4*>(Y + i * ldy)[c] = out;
+}
+
 // general (CSR) graph: one warp per row
 template <int CH>
 __global__ void __launch_bounds__(256)
@@ -276,6 +329,16 @@ rw_status rw_stencil_apply(const rw_graph* g, const float* X, int64_t ldx, float
                            int64_t ldz, float gamma, cudaStream_t st) {
   if (k <= 0 || k > 1024) return RW_ERR_INVALID_ARG;
   const int nch = (k + 3) / 4;
+  if (g->kind == RW_GRAPH_GRID && (int64_t)g->dims[0] * nch < ((int64_t)1 << 31) &&
+      g->dims[1] <= 65535 && g->dims[2] <= 65535) {
+    const dim3 grid(rw_blocks((int64_t)g->dims[0] * nch, 256), (unsigned)g->dims[1],
+                    (unsigned)g->dims[2]);
+    k_stencil_flat<<<grid, 256, 0, st>>>(X, ldx, Y, ldy, nch, g->cw, g->d, g->normalized,
+                                        g->ndim, g->dims[0], g->dims[1], g->dims[2], g->N,
+                                        alpha, beta, Z, ldz, gamma);
+    RW_LAUNCH_CHECK();
+    return RW_OK;
+  }
   const int ch = (nch + 31) / 32;
   switch (ch) {
     case 1: launch_wide<1>(g, X, ldx, Y, ldy, nch, alpha, beta, Z, ldz, gamma, st); break;
