@@ -45,6 +45,8 @@ WORKLOAD = "rwis-512x512-4label-voronoi"
 L2_FLUSH_BYTES = 256 << 20
 SEED_POOL = 400
 BETA_NEW = 150.0
+EIG_TOL = 4e-6   # residual tolerance of the offline eigensolver (512 x 512 basis)
+EIG_TOL_C3 = 1e-5   # the same at 128^3
 HBM_FALLBACK = 6800.0
 
 
@@ -342,7 +344,7 @@ def c3_block(rw, torch, dev, flush, stream, steps=100, quick=False, hbm=HBM_FALL
     N = int(np.prod(dims))
     g = rw.rw_build_graph(torch.from_numpy(J.astype(np.float32)).to(dev), dims, BETA)
     t0 = time.perf_counter()
-    b, info = rw.rw_precompute(g, 100, tol=1e-5, seed=1)
+    b, info = rw.rw_precompute(g, 100, tol=EIG_TOL_C3, seed=1)
     torch.cuda.synchronize()
     pre_s = time.perf_counter() - t0
     pool = [synth.sample_seeds(truth, dims, 500, 2, seed=synth.BASE_SEED + 2 + 7919 * (k + 1))
@@ -452,7 +454,7 @@ def beta_update_block(rw, torch, dev, g, b, J32, dims, truth, flush, stream, n_s
     upd_ms = ev0.elapsed_time(ev1)
     g2 = rw.rw_build_graph(J32, dims, BETA_NEW)
     t0 = time.perf_counter()
-    b2, info2 = rw.rw_precompute(g2, M, tol=1e-5, seed=1)
+    b2, info2 = rw.rw_precompute(g2, M, tol=EIG_TOL, seed=1)
     torch.cuda.synchronize()
     re_s = time.perf_counter() - t0
     conv = torch.empty(N, LABELS, device=dev)
@@ -523,6 +525,24 @@ def gpu_arm(args):
         with open(pk) as f:
             peaks = json.load(f)
 
+    if args.precompute_only:  # profiling runs of the offline eigensolver
+        out = {}
+        for name, (J_, dims_, _), m_ in (
+                ("512x512_m200", synth.voronoi_image(SIZE, SIZE, seed=synth.BASE_SEED + 1), M),
+                ("128x128x128_m100", synth.ellipsoid_volume(128, seed=synth.BASE_SEED + 2), 100)):
+            g_ = rw.rw_build_graph(torch.from_numpy(J_.astype(np.float32)).to(dev), dims_, BETA)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            b_, inf_ = rw.rw_precompute(g_, m_, tol=EIG_TOL if m_ == M else EIG_TOL_C3, seed=1)
+            torch.cuda.synchronize()
+            out[name] = {"seconds": time.perf_counter() - t0, **inf_}
+            rw.rw_basis_free(b_)
+            rw.rw_graph_free(g_)
+            if args.no_c3:
+                break
+        if rank == 0:
+            print(json.dumps(out))
+        return 0
     if args.stencil_only or args.pcg_only:  # profiling runs of one kernel
         out = {}
         J2, dims2, truth2 = synth.voronoi_image(SIZE, SIZE, seed=synth.BASE_SEED + 1)
@@ -564,7 +584,7 @@ def gpu_arm(args):
     J32 = torch.from_numpy(J.astype(np.float32)).to(dev)
     g = rw.rw_build_graph(J32, dims, BETA)
     t0 = time.perf_counter()
-    b, eig_info = rw.rw_precompute(g, M, tol=1e-5, seed=1)
+    b, eig_info = rw.rw_precompute(g, M, tol=EIG_TOL, seed=1)
     torch.cuda.synchronize()
     precompute_s = time.perf_counter() - t0
 
@@ -779,6 +799,8 @@ def main():
     ap.add_argument("--no-stencil", action="store_true", help="skip the stencil block")
     ap.add_argument("--stencil-only", action="store_true",
                     help="only time the Laplacian stencil (profiling runs)")
+    ap.add_argument("--precompute-only", action="store_true",
+                    help="only time the offline eigensolver (profiling runs)")
     ap.add_argument("--pcg-only", action="store_true",
                     help="only time 100 PCG iterations at 512^2 and 128^3 (profiling runs)")
     ap.add_argument("--no-beta-update", action="store_true",

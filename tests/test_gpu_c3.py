@@ -3,7 +3,8 @@ seeds per label): the eigenvector basis is certified by FP64 residuals and ortho
 oracle does not solve this eigenproblem); the online solve is compared with the oracle pipeline
 run on the same basis; the box-shaped weight change and the edge removal of Sec. III-B with the
 oracle's values; the adjoints (exact and eigenvector path) with central differences of GPU
-solves along beta and along a direction over the region-of-interest edges."""
+solves along beta and along a direction over the region-of-interest edges, and the exact
+adjoint with the FP64 oracle's gradient."""
 import time
 
 import numpy as np
@@ -207,3 +208,40 @@ def test_c3_fast_adjoint_beta_matches_differences(c3):
     finally:
         rw.rw_basis_free(b)
         rw.rw_graph_free(gg)
+
+
+def test_c3_exact_adjoint_matches_oracle_fp64_gradient(c3):
+    """rw_grad_exact at 128^3 against the FP64 oracle's gradient (forward and adjoint solved
+    by FP64 CG to 1e-10, stored by tests/golden/make_c3_adjoint.py): d loss / d beta and the
+    gradient on the 952 region-of-interest edges, within 1e-3 of the oracle's scale."""
+    import json
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "c3_adjoint_grad.json")
+    with open(path) as f:
+        ref = json.load(f)
+    dims, N, si, sl = c3["dims"], c3["N"], c3["si"], c3["sl"]
+    truth = c3["truth"].astype(np.float64)
+    free = np.ones(N, bool)
+    free[si] = False
+    P = _priors(c3)
+    sid, sld = to_dev(si), to_dev(sl)
+    U = torch.empty(N, 2, device=dev())
+    rw.rw_solve_pcg(c3["gg"], sid, sld, 2, U, priors=P, gamma=GAMMA, prior_mode=1,
+                    iters=20000, tol=1e-7)
+    loss, d = _loss(U.cpu().numpy(), truth, free)
+    # the FP32 solve's loss (measured 1.4e-4 relative above the FP64 one) only screens the setup
+    assert abs(loss - ref["loss"]) <= 1e-3 * abs(ref["loss"]), (loss, ref["loss"])
+    G = np.zeros((N, 2), np.float32)
+    G[free, 1] = 2 * d
+    gw = torch.empty(3 * N, device=dev())
+    gb = rw.rw_grad_exact(c3["gg"], sid, sld, 2, P, GAMMA, U, to_dev(G), gw, rel_tol=1e-7,
+                          max_iter=20000)
+    print(f"128^3 d loss/d beta: GPU {gb:.6e}, oracle FP64 {ref['dloss_dbeta']:.6e}")
+    assert abs(gb - ref["dloss_dbeta"]) <= 1e-3 * abs(ref["dloss_dbeta"])
+    ids = np.asarray(ref["edge_ids"], np.int64)
+    g_ref = np.asarray(ref["dloss_dw"])
+    g_gpu = gw.cpu().numpy().astype(np.float64)[ids]
+    err = np.abs(g_gpu - g_ref).max()
+    scale = np.abs(g_ref).max()
+    print(f"128^3 ROI edge gradient: max |d| = {err:.3e} of scale {scale:.3e}")
+    assert err <= 1e-3 * scale
