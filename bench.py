@@ -497,6 +497,121 @@ def beta_update_block(rw, torch, dev, g, b, J32, dims, truth, flush, stream, n_s
             "reference": "basic RW at beta = 150 by PCG to a relative residual of 1e-7"}
 
 
+BATCH_IMAGES, BATCH_ROUNDS, BATCH_M, BATCH_TOL, BATCH_STREAMS = 64, 8, 100, 1e-4, 8
+
+
+def batch_block(rw, torch, dev, repeats=3):
+    """Configuration 4, batched serving: 64 Voronoi images with sides drawn from U{128..512}
+    and 2-6 labels, each with its own basis (m = 100, precomputed offline, untimed), then 8
+    rounds of 10-50 new seeds per image (round 1 seeds every label), every round solving all 64
+    images (adaptive m <= 100, 3 refinement steps) through rw_batch_* on 8 streams.  Per round:
+    (a) direct: rw_batch_solve; (b) graph: the round captured into a CUDA graph (updated in
+    place after the first) and replayed.  The basis passes' launch shapes come from the
+    autotuner's table.  Latency of a round = host enqueue (or capture and update) plus device
+    time to completion; the 8-round sequence is repeated `repeats` times."""
+    shapes = rw.load_launch_shapes()
+    rng = np.random.default_rng(synth.BASE_SEED + 4)
+    images = []
+    t0 = time.perf_counter()
+    for k in range(BATCH_IMAGES):
+        side = int(rng.integers(128, 513))
+        L = int(rng.integers(2, 7))
+        J, dims, truth = synth.voronoi_image(side, side, n_regions=L,
+                                             seed=synth.BASE_SEED + 4 + 1000 * (k + 1))
+        g = rw.rw_build_graph(torch.from_numpy(J.astype(np.float32)).to(dev), dims, BETA)
+        b, info = rw.rw_precompute(g, BATCH_M, tol=BATCH_TOL, seed=k + 1)
+        # seeds: round 1 one voxel of every label plus random ones, later rounds random ones
+        by_label = [rng.permutation(np.nonzero(truth == c)[0]) for c in range(L)]
+        counts = rng.integers(10, 51, size=BATCH_ROUNDS)
+        chosen, used = [], set()
+        rounds = []
+        for r in range(BATCH_ROUNDS):
+            new = [int(by_label[c][0]) for c in range(L)] if r == 0 else []
+            while len(new) < counts[r]:
+                c = int(rng.integers(0, L))
+                cand = by_label[c][int(rng.integers(0, len(by_label[c])))]
+                if int(cand) not in used and int(cand) not in new:
+                    new.append(int(cand))
+            used.update(new)
+            chosen.extend(new)
+            si = np.array(chosen, dtype=np.int32)
+            sl = truth[si].astype(np.int32)
+            rounds.append((torch.from_numpy(si).to(dev), torch.from_numpy(sl).to(dev)))
+        N = side * side
+        images.append(dict(g=g, b=b, L=L, N=N, rounds=rounds, side=side,
+                           prob=torch.empty(N, L, device=dev),
+                           labels=torch.empty(N, dtype=torch.uint8, device=dev), eig=info))
+    torch.cuda.synchronize()
+    pre_s = time.perf_counter() - t0
+    kw = dict(gamma=GAMMA, m=0, m_step=M_STEP, eps=EPS, refine_steps=REFINE)
+    for im in images:   # size every workspace with the largest seed set, uncaptured
+        si, sl = im["rounds"][-1]
+        rw.rw_solve(im["g"], im["b"], si, sl, im["L"], im["prob"], im["labels"],
+                    want_info=False, **kw)
+    torch.cuda.synchronize()
+
+    def items(r):
+        return [dict(g=im["g"], b=im["b"], seed_idx=im["rounds"][r][0],
+                     seed_lab=im["rounds"][r][1], n_labels=im["L"], prob=im["prob"],
+                     labels=im["labels"]) for im in images]
+    bt = rw.rw_batch_create(BATCH_STREAMS)
+    stream = torch.cuda.Stream()
+    out = {}
+    try:
+        with torch.cuda.stream(stream):
+            for mode in ("direct", "graph"):
+                lat, host, dev_ms, upd = [], [], [], []
+                wall0 = time.perf_counter()
+                for rep in range(repeats + 1):   # the first pass is a warm-up
+                    for r in range(BATCH_ROUNDS):
+                        a = torch.cuda.Event(enable_timing=True)
+                        z = torch.cuda.Event(enable_timing=True)
+                        stream.synchronize()
+                        h0 = time.perf_counter()
+                        if mode == "direct":
+                            a.record(stream)
+                            rw.rw_batch_solve(bt, items(r), stream=stream, **kw)
+                        else:
+                            upd.append(rw.rw_batch_capture(bt, items(r), stream=stream, **kw))
+                            a.record(stream)
+                            rw.rw_batch_launch(bt, stream=stream)
+                        h1 = time.perf_counter()
+                        z.record(stream)
+                        stream.synchronize()
+                        h2 = time.perf_counter()
+                        if rep == 0:
+                            wall0 = time.perf_counter()
+                            continue
+                        lat.append(1000.0 * (h2 - h0))
+                        host.append(1000.0 * (h1 - h0))
+                        dev_ms.append(a.elapsed_time(z))
+                wall = time.perf_counter() - wall0
+                nmaps = BATCH_IMAGES * BATCH_ROUNDS * repeats
+                out[mode] = {"label_maps_per_s": nmaps / wall,
+                             "round_latency_ms_p50": float(np.percentile(lat, 50)),
+                             "round_latency_ms_p99": float(np.percentile(lat, 99)),
+                             "host_ms_per_round_p50": float(np.percentile(host, 50)),
+                             "device_ms_per_round_p50": float(np.percentile(dev_ms, 50)),
+                             "rounds_timed": len(lat)}
+                if mode == "graph":
+                    out[mode]["graph_updated_in_place"] = f"{sum(upd)}/{len(upd)}"
+    finally:
+        rw.rw_batch_free(bt)
+        for im in images:
+            rw.rw_basis_free(im["b"])
+            rw.rw_graph_free(im["g"])
+        rw.rw_set_launch_shape(0, 1, 1)
+    sides = [im["side"] for im in images]
+    labs = [im["L"] for im in images]
+    return {"workload": "rwis-batch-64-images-128..512-2..6labels-8rounds", "images": BATCH_IMAGES,
+            "rounds": BATCH_ROUNDS, "repeats": repeats, "streams": BATCH_STREAMS, "m_max": BATCH_M,
+            "side_min_max": [min(sides), max(sides)], "labels_min_max": [min(labs), max(labs)],
+            "precompute_s_total": pre_s, "eig_tol": BATCH_TOL,
+            "launch_shapes": [{k: e[k] for k in ("n_max", "proj_per_sm", "back_per_sm")}
+                              for e in shapes],
+            **out}
+
+
 def max_over_ranks(ms, world, device=None):
     """The slowest rank's time (every rank gets it); a no-op for one rank."""
     if world <= 1:
@@ -529,6 +644,11 @@ def gpu_arm(args):
         with open(pk) as f:
             peaks = json.load(f)
 
+    if args.batch_only:  # profiling runs of the batched-serving block
+        out = batch_block(rw, torch, dev, repeats=2)
+        if rank == 0:
+            print(json.dumps(out))
+        return 0
     if args.precompute_only:  # profiling runs of the offline eigensolver
         out = {}
         for name, (J_, dims_, _), m_ in (
@@ -747,6 +867,7 @@ def gpu_arm(args):
                          f"same seed sets as the GPU phase pass",
                "same_config": True,
                "adaptive_m_agreement": f"{agree}/{len(m_or)}"}
+    batched = None if args.no_batch else batch_block(rw, torch, dev)
     beta_upd = None if args.no_beta_update else beta_update_block(
         rw, torch, dev, g, b, J32, dims, truth, flush, stream)
     pcg_roof = pcg_roofline(N, 4, 2, pcg_ms / pcg_iters, hbm)
@@ -780,6 +901,7 @@ def gpu_arm(args):
         "c3_128cubed": c3,
         "stencil": stencil,
         "beta_update_512": beta_upd,
+        "batched_c4": batched,
     }
     rw.rw_basis_free(b)
     rw.rw_graph_free(g)
@@ -801,6 +923,9 @@ def main():
                     help="skip the e2e, PCG and CPU legs (profiling runs)")
     ap.add_argument("--no-c3", action="store_true", help="skip the 128^3 block")
     ap.add_argument("--no-stencil", action="store_true", help="skip the stencil block")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched-serving block")
+    ap.add_argument("--batch-only", action="store_true",
+                    help="only run the batched-serving block (profiling runs)")
     ap.add_argument("--stencil-only", action="store_true",
                     help="only time the Laplacian stencil (profiling runs)")
     ap.add_argument("--precompute-only", action="store_true",

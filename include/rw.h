@@ -385,6 +385,49 @@ rw_status rw_grad_fast(const rw_graph* g, const rw_basis* b, const int32_t* seed
 rw_status rw_rayleigh_quotients_noalloc(const rw_graph* g, const float* Q_dev, int64_t ldq,
                                         int32_t m, double* lambda_dev, void* stream);
 
+/* ------------------------------------------------------------------------------------------
+ * Batched solves for serving (the interactive use of Sec. I: users add seeds, labels are
+ * recomputed).  A batch handle owns n_streams CUDA streams.  rw_batch_solve runs rw_solve for
+ * every item (info not returned): the items are spread over the batch's streams, forked from
+ * and joined back into `stream`; items that share a graph handle go to the same stream (they
+ * share its workspace).  Every item's result is the one rw_solve gives alone, bit for bit.
+ * Errors: RW_ERR_INVALID_ARG for a bad item (nothing launched); the first failing solve's
+ * status otherwise (the streams are still joined).  opts->record_phases must be 0.
+ * rw_batch_capture records the same round into a CUDA graph held by the handle: the first
+ * capture instantiates it, later captures whose solves launch the same kernels update it in
+ * place (*updated_in_place = 1; new seed counts only change kernel arguments and grid sizes),
+ * others re-instantiate it.  rw_batch_launch replays the last captured round on `stream`; the
+ * seed and output buffers of the captured items must still be valid.  Capture needs a
+ * non-default stream and scratch already sized: run each graph once, uncaptured, with at least
+ * as many seeds and the same label count first (a scratch allocation inside the capture fails
+ * it with RW_ERR_OOM or RW_ERR_CUDA).  The process-wide kernel-launch counter counts captured
+ * launches at capture, not at replay.
+ * rw_set_launch_shape sets the blocks per SM of the two 16-bit basis passes for graphs with
+ * N <= n_max (up to 16 size classes, ascending; n_max <= 0 clears the table); without an entry
+ * the projection uses 2 and the back-projection 3.  proj_per_sm in [1, 4], back_per_sm in
+ * [1, 8].  The project's autotuner (paper_1607_04174_gb300/autotune.py) measures the table.
+ * ---------------------------------------------------------------------------------------- */
+typedef struct rw_batch rw_batch;
+typedef struct rw_batch_item {
+  const rw_graph* g;
+  const rw_basis* b;
+  const int32_t* seed_idx_dev;
+  const int32_t* seed_lab_dev;
+  int32_t S;
+  int32_t n_labels;
+  const float* priors_dev;   /* NULL unless opts->prior_mode == 1 */
+  float* prob_dev;           /* N x n_labels */
+  uint8_t* labels_dev;       /* N or NULL */
+} rw_batch_item;
+rw_status rw_batch_create(int32_t n_streams, rw_batch** out);
+void rw_batch_free(rw_batch* bt);
+rw_status rw_batch_solve(rw_batch* bt, const rw_batch_item* items, int32_t n,
+                         const rw_solve_opts* opts, void* stream);
+rw_status rw_batch_capture(rw_batch* bt, const rw_batch_item* items, int32_t n,
+                           const rw_solve_opts* opts, void* stream, int32_t* updated_in_place);
+rw_status rw_batch_launch(rw_batch* bt, void* stream);
+rw_status rw_set_launch_shape(int64_t n_max, int32_t proj_per_sm, int32_t back_per_sm);
+
 /* Writes the Gaussian-fit priors of Sec. IV-A (N x n_labels, node-major) for the seeds. */
 rw_status rw_solve_priors(const rw_graph* g, const int32_t* seed_idx_dev,
                           const int32_t* seed_lab_dev, int32_t S, int32_t n_labels,

@@ -313,3 +313,80 @@ def rw_basis_load(g, path, m_load=0, stream=None):
     _check(abi.lib().rw_basis_load(g, str(path).encode(), m_load, _stream(stream), C.byref(h)),
            "rw_basis_load")
     return h.value
+
+
+# ----------------------------------------------------------------------------- batched serving
+
+
+def rw_batch_create(n_streams=8):
+    h = C.c_void_p()
+    _check(abi.lib().rw_batch_create(n_streams, C.byref(h)), "rw_batch_create")
+    return h.value
+
+
+def rw_batch_free(bt):
+    abi.lib().rw_batch_free(bt)
+
+
+def _batch_items(items):
+    """items: sequence of dicts with g, b, seed_idx, seed_lab, n_labels, prob, and optionally
+    labels and priors (CUDA tensors)."""
+    arr = (abi.rw_batch_item * len(items))()
+    for k, it in enumerate(items):
+        a = arr[k]
+        a.g, a.b = it["g"], it["b"]
+        a.seed_idx_dev, a.seed_lab_dev = _dp(it["seed_idx"]), _dp(it["seed_lab"])
+        a.S = len(it["seed_idx"])
+        a.n_labels = it["n_labels"]
+        a.priors_dev = _dp(it.get("priors"))
+        a.prob_dev = _dp(it["prob"])
+        a.labels_dev = _dp(it.get("labels"))
+    return arr
+
+
+def rw_batch_solve(bt, items, gamma=1e-3, m=0, m_step=10, eps=0.1, refine_steps=3,
+                   refine_mode=abi.RW_REFINE_JACOBI, omega=0.8, basis_format=abi.RW_BASIS_F16,
+                   prior_mode=0, stream=None):
+    o = _solve_opts(gamma, m, m_step, eps, refine_steps, refine_mode, omega, basis_format,
+                    prior_mode)
+    arr = _batch_items(items)
+    return _check(abi.lib().rw_batch_solve(bt, arr, len(items), C.byref(o), _stream(stream)),
+                  "rw_batch_solve")
+
+
+def rw_batch_capture(bt, items, gamma=1e-3, m=0, m_step=10, eps=0.1, refine_steps=3,
+                     refine_mode=abi.RW_REFINE_JACOBI, omega=0.8, basis_format=abi.RW_BASIS_F16,
+                     prior_mode=0, stream=None):
+    """Returns 1 when the held graph was updated in place, 0 when it was instantiated."""
+    o = _solve_opts(gamma, m, m_step, eps, refine_steps, refine_mode, omega, basis_format,
+                    prior_mode)
+    arr = _batch_items(items)
+    upd = C.c_int32(0)
+    _check(abi.lib().rw_batch_capture(bt, arr, len(items), C.byref(o), _stream(stream),
+                                      C.byref(upd)), "rw_batch_capture")
+    return upd.value
+
+
+def rw_batch_launch(bt, stream=None):
+    return _check(abi.lib().rw_batch_launch(bt, _stream(stream)), "rw_batch_launch")
+
+
+def rw_set_launch_shape(n_max, proj_per_sm, back_per_sm):
+    return _check(abi.lib().rw_set_launch_shape(n_max, proj_per_sm, back_per_sm),
+                  "rw_set_launch_shape")
+
+
+def load_launch_shapes(path=None):
+    """Installs the launch-shape table measured by the project's autotuner
+    (paper_1607_04174_gb300/autotune.py); returns the entries installed."""
+    import json
+    import os
+    path = path or os.path.join(os.path.dirname(os.path.abspath(__file__)), "launch_shapes.json")
+    if not os.path.exists(path):
+        return []
+    with open(path) as f:
+        table = json.load(f)
+    rw_set_launch_shape(0, 1, 1)
+    for e in table["entries"]:
+        rw_set_launch_shape(int(e["n_max"]), int(e["proj_per_sm"]), int(e["back_per_sm"]))
+    return table["entries"]

@@ -75,6 +75,12 @@ class rw_topology_update(C.Structure):
                 ("etabar_val_dev", C.c_void_p)]
 
 
+class rw_batch_item(C.Structure):
+    _fields_ = [("g", C.c_void_p), ("b", C.c_void_p), ("seed_idx_dev", C.c_void_p),
+                ("seed_lab_dev", C.c_void_p), ("S", C.c_int32), ("n_labels", C.c_int32),
+                ("priors_dev", C.c_void_p), ("prob_dev", C.c_void_p), ("labels_dev", C.c_void_p)]
+
+
 P = C.c_void_p
 I32, I64, D = C.c_int32, C.c_int64, C.c_double
 HP = C.POINTER(C.c_void_p)
@@ -109,6 +115,13 @@ PROTOTYPES = {
     "rw_rayleigh_quotients_noalloc": (I32, [P, P, I64, I32, P, P]),
     "rw_block_gram_scratch_bytes": (C.c_size_t, [I64, I32, I32]),
     "rw_basis_save": (I32, [P, C.c_char_p, P]),
+    "rw_batch_create": (I32, [I32, HP]),
+    "rw_batch_free": (None, [P]),
+    "rw_batch_solve": (I32, [P, C.POINTER(rw_batch_item), I32, C.POINTER(rw_solve_opts), P]),
+    "rw_batch_capture": (I32, [P, C.POINTER(rw_batch_item), I32, C.POINTER(rw_solve_opts), P,
+                               C.POINTER(I32)]),
+    "rw_batch_launch": (I32, [P, P]),
+    "rw_set_launch_shape": (I32, [I64, I32, I32]),
     "rw_basis_load": (I32, [P, C.c_char_p, I32, P, HP]),
     "rw_block_gram": (I32, [P, I64, P, I64, I64, I32, I32, P, I32, P, C.c_size_t, P]),
 }

@@ -1339,11 +1339,14 @@ __device__ void adapt_body(const float* __restrict__ G, int ldg, const float* __
       __syncthreads();
       for (int k = 0; k < L && okc; ++k) {
         if (!(nk[k] > (float)rho)) continue;
+        // Newton from the left converges quadratically; in FP32 an ill-conditioned G_m + mu I
+        // can keep ||a|| from settling below 1e-5 rho, so stop at 1e-4 rho or after 12 steps
+        // (each step refactors the m x m matrix on one CTA; 40 steps cost milliseconds)
         float mu = mu0;
-        for (int it = 0; it < 40; ++it) {
+        for (int it = 0; it < 12; ++it) {
           __syncthreads();
           const float na = nk[k];
-          if (fabsf(na - (float)rho) <= 1e-5f * (float)rho) break;
+          if (fabsf(na - (float)rho) <= 1e-4f * (float)rho) break;
           if (warp == 0) {  // ||q||^2 with L q = a
             fwd_lower_warp(B2, m, mss, al + k * mmax, bb + k * mmax);
             float s2 = 0.f;
@@ -2887,6 +2890,45 @@ rw_status launch_priors(const rw_graph* g, int L, int prior_mode, const float* p
   return RW_OK;
 }
 
+// Launch shapes of the two 16-bit basis passes (blocks per SM), per graph-size class: entry k
+// applies to graphs with N <= nmax_k (the first such entry, classes ascending).  Set by
+// rw_set_launch_shape from a table the project's autotuner measures; without an entry the
+// projection takes 2 blocks per SM and the back-projection 3.
+namespace {
+struct ShapeEntry { int64_t nmax; int proj, back; };
+std::mutex g_shape_mu;
+ShapeEntry g_shapes[16];
+int g_nshapes = 0;
+
+void launch_shape(int64_t N, int* proj, int* back) {
+  std::lock_guard<std::mutex> lock(g_shape_mu);
+  *proj = 2;
+  *back = 3;
+  for (int k = 0; k < g_nshapes; ++k)
+    if (N <= g_shapes[k].nmax) { *proj = g_shapes[k].proj; *back = g_shapes[k].back; return; }
+}
+}  // namespace
+
+extern "C" rw_status rw_set_launch_shape(int64_t n_max, int32_t proj_per_sm,
+                                         int32_t back_per_sm) {
+  std::lock_guard<std::mutex> lock(g_shape_mu);
+  if (n_max <= 0) { g_nshapes = 0; return RW_OK; }
+  if (proj_per_sm < 1 || proj_per_sm > 4 || back_per_sm < 1 || back_per_sm > 8)
+    return RW_ERR_INVALID_ARG;
+  int k = 0;
+  while (k < g_nshapes && g_shapes[k].nmax < n_max) ++k;
+  if (k < g_nshapes && g_shapes[k].nmax == n_max) {
+    g_shapes[k].proj = proj_per_sm;
+    g_shapes[k].back = back_per_sm;
+    return RW_OK;
+  }
+  if (g_nshapes == 16) return RW_ERR_INVALID_ARG;
+  for (int j = g_nshapes; j > k; --j) g_shapes[j] = g_shapes[j - 1];
+  g_shapes[k] = ShapeEntry{n_max, proj_per_sm, back_per_sm};
+  ++g_nshapes;
+  return RW_OK;
+}
+
 static rw_status validate_solve(const rw_graph* g, const rw_basis* b, const int32_t* si,
                                 const int32_t* sl, int S, int L, const float* priors,
                                 const rw_solve_opts* o, const void* prob) {
@@ -3038,9 +3080,11 @@ extern "C" rw_status rw_solve(const rw_graph* g, const rw_basis* b, const int32_
     RW_LAUNCH_CHECK();
   }
   int ldq_e = fmt == RW_BASIS_F32 ? b->ld32 : b->ld16;
-  // projection blocks: the chunk-major 16-bit kernel takes 2 per SM (more rows per block, fewer
-  // partials to add); the FP32 row kernel 4 per SM
-  const int nblk_p = fmt == RW_BASIS_F32 ? nblk : 2 * sms;
+  // projection blocks: the chunk-major 16-bit kernel takes the tuned count per SM (2 by
+  // default: more rows per block, fewer partials to add); the FP32 row kernel 4 per SM
+  int proj_per_sm = 2, back_per_sm = 3;
+  launch_shape(g->N, &proj_per_sm, &back_per_sm);
+  const int nblk_p = fmt == RW_BASIS_F32 ? nblk : proj_per_sm * sms;
   float zscale = fmt == RW_BASIS_F16 ? 1.f / b->qscale : 1.f;
   float cscale = fmt == RW_BASIS_F16 ? 1.f / b->qscale : 1.f;
   if (fmt == RW_BASIS_F16)
@@ -3090,7 +3134,7 @@ extern "C" rw_status rw_solve(const rw_graph* g, const rw_basis* b, const int32_
   }
   RW_TRY(mark(5));
   // back-projection (+ refinement); the 16-bit kernel holds three blocks per SM
-  const int nblk_b = fmt == RW_BASIS_F32 ? nblk : 3 * sms;
+  const int nblk_b = fmt == RW_BASIS_F32 ? nblk : back_per_sm * sms;
   const int steps = opts->refine_steps;
   float* xh0 = nullptr;
   float* xh1 = nullptr;

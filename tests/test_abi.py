@@ -62,6 +62,8 @@ def test_struct_layouts_match_c(tmp_path):
                              "n_edges"],
         "rw_topology_update": ["kind", "naive", "edge_ids_dev", "n_edges", "n_bar",
                                "eta_rowptr_dev", "eta_col_dev", "eta_val_dev", "etabar_val_dev"],
+        "rw_batch_item": ["g", "b", "seed_idx_dev", "seed_lab_dev", "S", "n_labels",
+                          "priors_dev", "prob_dev", "labels_dev"],
     }
     lines = ['#include <stdio.h>', '#include <stddef.h>', f'#include "{HEADER}"', "int main(){"]
     for s, fields in structs.items():
@@ -102,7 +104,7 @@ def test_null_handles_are_refused_on_the_host(lib):
     from paper_1607_04174_gb300 import abi
     before = lib.rw_kernel_launches()
     status_calls = [n for n, (res, _) in abi.PROTOTYPES.items()
-                    if res is C.c_int32 and n != "rw_basis_m"]
+                    if res is C.c_int32 and n not in ("rw_basis_m", "rw_set_launch_shape")]
     assert len(status_calls) >= 17
     for name in status_calls:
         st = getattr(lib, name)(*_null_args(abi.PROTOTYPES[name][1]))
@@ -110,13 +112,18 @@ def test_null_handles_are_refused_on_the_host(lib):
     assert lib.rw_basis_m(None) == 0
     assert lib.rw_graph_num_nodes(None) == 0
     assert lib.rw_block_gram_scratch_bytes(1, 0, 1) == 0
+    assert lib.rw_set_launch_shape(4096, 0, 3) == -1      # a shape out of range
+    assert lib.rw_set_launch_shape(4096, 1, 9) == -1
+    assert lib.rw_set_launch_shape(0, 1, 1) == 0          # clears the (host-side) table
+    lib.rw_batch_free(None)
     assert lib.rw_block_gram_scratch_bytes(2048, 128, 256) == 256 + 4 * 128 * 256 * 2
     lib.rw_graph_free(None)
     lib.rw_basis_free(None)
     assert lib.rw_kernel_launches() == before
     # every declared entry point is one of the calls above or an accessor checked elsewhere
     covered = set(status_calls) | {"rw_basis_m", "rw_graph_num_nodes", "rw_graph_free",
-                                   "rw_block_gram_scratch_bytes",
+                                   "rw_block_gram_scratch_bytes", "rw_set_launch_shape",
+                                   "rw_batch_free",
                                    "rw_basis_free", "rw_status_str", "rw_last_error_message",
                                    "rw_kernel_launches"}
     assert set(_declared()) <= covered, sorted(set(_declared()) - covered)
