@@ -214,3 +214,31 @@ def pick_edges(ids, fraction, seed):
     rng = np.random.default_rng(seed)
     k = int(round(fraction * ids.size))
     return np.sort(rng.choice(ids, size=k, replace=False)).astype(np.int64)
+
+
+# ----------------------------------------------------------------------------- registration
+
+
+def registration_pair(n=96, seed=BASE_SEED + 5, max_disp=2.0, smooth=3.0, sigma=0.03,
+                      field_smooth=8.0):
+    """Fixed / moving volumes of side n: fixed is a smoothed random field in [0, 1] plus noise
+    sigma; the displacement u (N x 3, components x, y, z) is a Gaussian-smoothed random vector
+    field scaled so that max |u| = max_disp voxels; moving(x) = fixed(x + u(x)) by trilinear
+    interpolation (nearest voxel outside), plus its own noise.  Returns (fixed, moving, dims, u)
+    as flat float64 arrays, x fastest."""
+    rng = np.random.default_rng(seed)
+    dims = (n, n, n)
+    base = ndimage.gaussian_filter(rng.standard_normal((n, n, n)), smooth)
+    base = (base - base.min()) / max(base.max() - base.min(), 1e-12)
+    comp = [ndimage.gaussian_filter(rng.standard_normal((n, n, n)), field_smooth)
+            for _ in range(3)]                      # x, y, z components, arrays indexed [z, y, x]
+    mag = np.sqrt(sum(c * c for c in comp))
+    scale = max_disp / max(mag.max(), 1e-12)
+    comp = [c * scale for c in comp]
+    z, y, x = np.indices((n, n, n), dtype=np.float64)
+    coords = [z + comp[2], y + comp[1], x + comp[0]]
+    moving = ndimage.map_coordinates(base, coords, order=1, mode="nearest")
+    fixed = np.clip(base + sigma * rng.standard_normal(base.shape), 0.0, 1.0)
+    moving = np.clip(moving + sigma * rng.standard_normal(base.shape), 0.0, 1.0)
+    u = np.stack([c.ravel() for c in comp], axis=1)
+    return fixed.ravel(), moving.ravel(), dims, u
