@@ -428,6 +428,33 @@ rw_status rw_batch_capture(rw_batch* bt, const rw_batch_item* items, int32_t n,
 rw_status rw_batch_launch(rw_batch* bt, void* stream);
 rw_status rw_set_launch_shape(int64_t n_max, int32_t proj_per_sm, int32_t back_per_sm);
 
+/* ------------------------------------------------------------------------------------------
+ * Registration (RWIR, Sec. II-A: the K labels are displacement vectors; Sec. III-A-2; Sec. IV-B).
+ * rw_registration_priors: P (N x K, node-major) for the fixed / moving images (N floats each,
+ * device, same grid) and the K displacements disp_dev (K x ndim int32, device, voxels): the sum
+ * of absolute differences between fixed(x + o) and moving(x + o + d_k) over the patch offsets
+ * o in [-half, half]^ndim (coordinates clamped into the grid), squared, negated, exponentiated
+ * and normalized to sum to 1 over the labels at each voxel.  dims[0..ndim-1] as for graphs;
+ * 1 <= K <= 4096, 0 <= half <= 8.  Asynchronous.
+ * rw_solve_unseeded: the fast RW with priors and no seeds, Eq. (U_lin_comb) with S = 0:
+ * U-hat = Q Lambda_gamma (gamma Q^T P-hat), then opts->refine_steps damped-Jacobi steps of
+ * Eq. (rw_eq) (no seeded rows).  opts->m = 0 chooses m by Eq. (g): the first candidate
+ * m_step, 2 m_step, ..., m_max with max_k ||p-hat_k - Q_m Q_m^T p-hat_k||^2 <= 1^T D 1 eps^2
+ * (every label evaluated); otherwise m = opts->m.  prob_dev: N x K; labels_dev (N, K <= 255,
+ * or NULL): the most probable label; field_dev (N x disp_dim, or NULL): the expected
+ * displacement sum_k U_k d_k with disp_dev (K x disp_dim).  Labels run in chunks of 8 through
+ * the basis passes; 1 <= K <= 4096.  16-bit or FP32 basis (BF16: RW_ERR_UNSUPPORTED).  m_used
+ * (host, or NULL): the m taken; when given the call synchronizes and reports device errors.
+ * Scratch: grown in the graph handle (about 3 N x 8 floats plus the m_max x K projections).
+ * ---------------------------------------------------------------------------------------- */
+rw_status rw_registration_priors(const float* fixed_dev, const float* moving_dev, int32_t ndim,
+                                 const int32_t* dims, const int32_t* disp_dev, int32_t K,
+                                 int32_t half, float* priors_dev, void* stream);
+rw_status rw_solve_unseeded(const rw_graph* g, const rw_basis* b, const float* priors_dev,
+                            int32_t K, const rw_solve_opts* opts, float* prob_dev,
+                            uint8_t* labels_dev, const int32_t* disp_dev, int32_t disp_dim,
+                            float* field_dev, int32_t* m_used, void* stream);
+
 /* Writes the Gaussian-fit priors of Sec. IV-A (N x n_labels, node-major) for the seeds. */
 rw_status rw_solve_priors(const rw_graph* g, const int32_t* seed_idx_dev,
                           const int32_t* seed_lab_dev, int32_t S, int32_t n_labels,

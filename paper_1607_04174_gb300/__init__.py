@@ -390,3 +390,30 @@ def load_launch_shapes(path=None):
     for e in table["entries"]:
         rw_set_launch_shape(int(e["n_max"]), int(e["proj_per_sm"]), int(e["back_per_sm"]))
     return table["entries"]
+
+
+# ----------------------------------------------------------------------------- registration
+
+
+def rw_registration_priors(fixed, moving, dims, disp, priors, half=2, stream=None):
+    """priors (N x K float32, CUDA) from the fixed and moving images (N float32, CUDA) and the
+    K x ndim int32 displacements disp (CUDA)."""
+    d = (C.c_int32 * 3)(*(list(int(v) for v in dims) + [1] * (3 - len(dims))))
+    return _check(abi.lib().rw_registration_priors(_dp(fixed), _dp(moving), len(dims), d,
+                                                   _dp(disp), disp.shape[0], half, _dp(priors),
+                                                   _stream(stream)), "rw_registration_priors")
+
+
+def rw_solve_unseeded(g, b, priors, prob, labels=None, disp=None, field=None, gamma=1.0, m=0,
+                      m_step=10, eps=0.1, refine_steps=3, omega=0.8,
+                      basis_format=abi.RW_BASIS_F16, want_m=True, stream=None):
+    """Returns the m used (want_m) or None."""
+    o = _solve_opts(gamma, m, m_step, eps, refine_steps, abi.RW_REFINE_JACOBI, omega,
+                    basis_format, 1)
+    mu = C.c_int32(0)
+    _check(abi.lib().rw_solve_unseeded(g, b, _dp(priors), priors.shape[1], C.byref(o), _dp(prob),
+                                       _dp(labels), _dp(disp),
+                                       0 if disp is None else disp.shape[1], _dp(field),
+                                       C.byref(mu) if want_m else None, _stream(stream)),
+           "rw_solve_unseeded")
+    return mu.value if want_m else None

@@ -372,7 +372,7 @@ static void graph_release(rw_graph* g) {
   cudaFree(g->sq); cudaFree(g->status); cudaFree(g->rowptr); cudaFree(g->col);
   cudaFree(g->wcsr); cudaFree(g->ccsr);
   g->ws.seedlab.release(); g->ws.seedpart.release(); g->ws.small.release(); g->ws.xhat[0].release();
-  g->ws.xhat[1].release(); g->ws.phat.release(); g->ws.pcg.release(); g->ws.stage.release(); g->ws.grad.release(); g->ws.host.release();
+  g->ws.xhat[1].release(); g->ws.phat.release(); g->ws.pcg.release(); g->ws.stage.release(); g->ws.grad.release(); g->ws.reg.release(); g->ws.host.release();
   for (auto& e : g->ws.ev) if (e) cudaEventDestroy(e);
   g->upd.release();
   delete g;

@@ -105,6 +105,7 @@ struct SolveWorkspace {
   DevBuf pcg;       // PCG vectors
   DevBuf stage;     // device staging of the host-buffer entry point
   DevBuf grad;      // fast-path gradient scratch (grown on first use)
+  DevBuf reg;       // unseeded (registration) solve: one label chunk of U, N x lpad FP32
   PinnedBuf host;   // info readback
   cudaEvent_t ev[8] = {};  // phase timing events (created on first use)
   int64_t small_cap_S = 0, small_cap_m = 0;

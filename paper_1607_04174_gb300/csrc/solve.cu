@@ -3275,3 +3275,292 @@ extern "C" rw_status rw_solve_priors(const rw_graph* g, const int32_t* seed_idx_
   RW_TRY(rw_unhat_priors(g, phat, lp, n_labels, priors_dev, st));
   return rw_last_device_status(g, stream);
 }
+
+// ---------------------------------------------------------------------------------------
+// Unseeded solve (registration, Sec. II-A with no landmarks): with S = 0, Eq. (U_lin_comb)
+// reads U-hat = Q Lambda_gamma (gamma Z), Z = Q^T P-hat, and the refinement is the damped
+// Jacobi of Eq. (rw_eq) without seeded rows.  The K labels (displacements) run in chunks of
+// lp = 8 (4 when K <= 4) through the same basis passes; m is given or chosen by Eq. (g),
+// g_k(m) = ||p-hat_k||^2 - ||Z_k[:m]||^2 (Q orthonormal), the smallest candidate with
+// max_k g_k <= g_max = 1^T D 1 eps^2 (normalized form).
+// ---------------------------------------------------------------------------------------
+namespace {
+
+// P-hat chunk: phat[i][j] = d_i^{1/2} P[i][k0 + j] (j < Lc, zero above); optionally the squared
+// norms of the chunk's P-hat columns, per block in FP64, one atomic per block and label.
+__global__ void __launch_bounds__(256)
+k_hat_chunk(const float* __restrict__ P, int K, int k0, int Lc, int lp,
+            const float* __restrict__ sq, int64_t N, float* __restrict__ phat,
+            double* __restrict__ pnorm) {
+  __shared__ double red[8][8];
+  double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const float s = sq[i];
+    for (int j = 0; j < lp; ++j) {
+      const float v = j < Lc ? s * P[i * K + k0 + j] : 0.f;
+      phat[i * lp + j] = v;
+      acc[j] += (double)v * v;
+    }
+  }
+  if (!pnorm) return;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int j = 0; j < 8; ++j) {
+    double v = acc[j];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) red[w][j] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < Lc) {
+    double t = 0.0;
+    for (int ww = 0; ww < 8; ++ww) t += red[ww][threadIdx.x];
+    atomicAdd(&pnorm[k0 + threadIdx.x], t);
+  }
+}
+
+__global__ void k_store_z(const float* __restrict__ Z, int lp, int Lc, int k0, int rows, int K,
+                          float* __restrict__ Zall) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= rows * Lc) return;
+  const int i = e / Lc, j = e - i * Lc;
+  Zall[(int64_t)i * K + k0 + j] = Z[i * lp + j];
+}
+
+// Eq. (g) over the candidates m_step, 2 m_step, ..., m_max: running sums of Z^2 per label in
+// FP64, first candidate whose worst label passes (m_max, flagged, when none does)
+__global__ void __launch_bounds__(256)
+k_choose_m_g(const float* __restrict__ Zall, int K, int m_max, int m_step,
+             const double* __restrict__ pnorm, double gmax, int* __restrict__ mdev,
+             double* __restrict__ gout) {
+  __shared__ double wmax[8];
+  __shared__ int done;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (threadIdx.x == 0) done = 0;
+  int m_prev = 0;
+  for (int mc = m_step < m_max ? m_step : m_max;; mc = (mc + m_step < m_max ? mc + m_step : m_max)) {
+    double worst = 0.0;
+    for (int k = threadIdx.x; k < K; k += blockDim.x) {
+      double c = 0.0;
+      for (int i = m_prev; i < mc; ++i) {
+        const double z = Zall[(int64_t)i * K + k];
+        c += z * z;
+      }
+      gout[k] = (m_prev == 0 ? pnorm[k] : gout[k]) - c;
+      worst = fmax(worst, gout[k]);
+    }
+    for (int o = 16; o > 0; o >>= 1) worst = fmax(worst, __shfl_xor_sync(0xffffffffu, worst, o));
+    __syncthreads();
+    if (lane == 0) wmax[w] = worst;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int ww = 0; ww < (int)(blockDim.x >> 5); ++ww) t = fmax(t, wmax[ww]);
+      if (t <= gmax || mc == m_max) {
+        mdev[0] = mc;
+        mdev[1] = t <= gmax ? 0 : 1;
+        done = 1;
+      }
+    }
+    __syncthreads();
+    if (done) return;
+    m_prev = mc;
+  }
+}
+
+// C = gamma Lambda_gamma Z[:m] for one chunk (rows >= m and labels >= Lc zero)
+__global__ void k_c_unseeded(const float* __restrict__ Zall, int K, int k0, int Lc, int lp,
+                             const double* __restrict__ lam, double gamma,
+                             const int* __restrict__ mdev, int rows, float* __restrict__ C) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= rows * lp) return;
+  const int i = e / lp, j = e - i * lp;
+  const int m = mdev[0];
+  C[e] = (i < m && j < Lc) ? (float)(gamma * Zall[(int64_t)i * K + k0 + j] / (lam[i] + gamma))
+                           : 0.f;
+}
+
+__global__ void k_scatter_cols(const float* __restrict__ Uc, int Lc, int64_t N,
+                               float* __restrict__ prob, int K, int k0) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= N * Lc) return;
+  const int64_t i = e / Lc;
+  const int j = (int)(e - i * Lc);
+  prob[i * K + k0 + j] = Uc[e];
+}
+
+// hard labels (largest probability, ties to the lowest label) and the expected displacement
+__global__ void k_reg_finish(const float* __restrict__ prob, int K, int64_t N,
+                             uint8_t* __restrict__ labels, const int32_t* __restrict__ disp,
+                             int dd, float* __restrict__ field) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const float* p = prob + i * K;
+  int best = 0;
+  float bv = -INFINITY;
+  float f[3] = {0.f, 0.f, 0.f};
+  for (int k = 0; k < K; ++k) {
+    const float u = p[k];
+    if (u > bv) { bv = u; best = k; }
+    if (field)
+      for (int a = 0; a < dd; ++a) f[a] = fmaf(u, (float)disp[k * dd + a], f[a]);
+  }
+  if (labels) labels[i] = (uint8_t)best;
+  if (field)
+    for (int a = 0; a < dd; ++a) field[i * dd + a] = f[a];
+}
+
+}  // namespace
+
+template <typename T>
+static rw_status unseeded_passes(const rw_graph* g, const rw_basis* b, const T* Q, int ldq,
+                                 float zscale, float cscale, const float* priors, int K, int lp,
+                                 const rw_solve_opts* opts, float* prob, cudaStream_t st,
+                                 int* mall, int* mdev, float* Z, float* lgam, float* C,
+                                 float* Zall, double* pnorm, double* gout, float* part,
+                                 int mq, int nblk_p, int nblk_b) {
+  rw_graph* gm = const_cast<rw_graph*>(g);
+  SolveWorkspace& ws = gm->ws;
+  const int64_t N = g->N;
+  const double gamma = opts->gamma;
+  const bool adaptive = opts->m == 0;
+  const int m_max = adaptive ? b->m : opts->m;
+  const int steps = opts->refine_steps;
+  const float omega = (float)(opts->omega > 0 ? std::min(opts->omega, 1.0) : 0.8);
+  const int nchunks = (K + lp - 1) / lp;
+  float* phat = ws.phat.as<float>();
+  int* seedlab = ws.seedlab.as<int>();
+  const int sms = g_rw_num_sms > 0 ? g_rw_num_sms : 148;
+  const unsigned hblk = (unsigned)std::min<int64_t>(rw_blocks(N, 256), 4 * sms);
+  // Z of every chunk over all m_max columns (and the norms of P-hat for Eq. g)
+  RW_CHECK_CUDA(cudaMemsetAsync(pnorm, 0, sizeof(double) * K, st));
+  RW_LAUNCH(k_set_m, 1, 32, 0, st, mall, m_max);
+  for (int c = 0; c < nchunks; ++c) {
+    const int k0 = c * lp, Lc = std::min(lp, K - k0);
+    k_hat_chunk<<<hblk, 256, 0, st>>>(priors, K, k0, Lc, lp, g->sq, N, phat,
+                                      adaptive ? pnorm : nullptr);
+    RW_LAUNCH_CHECK();
+    RW_TRY(proj_back<T>(lp, false, Q, ldq, phat, seedlab, g, mall, part, nblk_p, nullptr, 0.f,
+                        nullptr, nullptr, nullptr, Lc, st));
+    RW_LAUNCH(k_reduce_partials, rw_blocks((int64_t)std::max(mq * lp, m_max) * 32, 256), 256, 0,
+              st, part, nblk_p, ldq, lp, mq, zscale, Z, b->lam, gamma, m_max, lgam);
+    k_store_z<<<rw_blocks((int64_t)m_max * Lc, 256), 256, 0, st>>>(Z, lp, Lc, k0, m_max, K, Zall);
+    RW_LAUNCH_CHECK();
+  }
+  if (adaptive) {
+    const int m_step = opts->m_step > 0 ? opts->m_step : 10;
+    const double eps = opts->eps > 0 ? opts->eps : 0.1;
+    const double gmax = (g->normalized ? g->dsum : (double)N) * eps * eps;
+    k_choose_m_g<<<1, 256, 0, st>>>(Zall, K, m_max, m_step, pnorm, gmax, mdev, gout);
+    RW_LAUNCH_CHECK();
+  } else {
+    RW_LAUNCH(k_set_m, 1, 32, 0, st, mdev, m_max);
+  }
+  float* xh0 = steps > 0 ? ws.xhat[0].as<float>() : nullptr;
+  float* xh1 = steps > 0 ? ws.xhat[1].as<float>() : nullptr;
+  float* Uc = ws.reg.as<float>();
+  for (int c = 0; c < nchunks; ++c) {
+    const int k0 = c * lp, Lc = std::min(lp, K - k0);
+    k_hat_chunk<<<hblk, 256, 0, st>>>(priors, K, k0, Lc, lp, g->sq, N, phat, nullptr);
+    RW_LAUNCH_CHECK();
+    k_c_unseeded<<<rw_blocks((int64_t)mq * lp, 256), 256, 0, st>>>(Zall, K, k0, Lc, lp, b->lam,
+                                                                 gamma, mdev, mq, C);
+    RW_LAUNCH_CHECK();
+    RW_TRY(proj_back<T>(lp, true, Q, ldq, phat, seedlab, g, mdev, part, nblk_b, C, cscale, xh0,
+                        steps > 0 ? nullptr : Uc, nullptr, Lc, st));
+    if (steps > 0) {
+      float* a = xh0;
+      float* o = xh1;
+      for (int t = 0; t < steps; ++t) {
+        const int last = t == steps - 1;
+        RW_TRY(jacobi(g, lp, a, o, phat, seedlab, Lc, (float)gamma, omega, last,
+                      last ? Uc : nullptr, nullptr, nullptr, st));
+        std::swap(a, o);
+      }
+    }
+    k_scatter_cols<<<rw_blocks(N * Lc, 256), 256, 0, st>>>(Uc, Lc, N, prob, K, k0);
+    RW_LAUNCH_CHECK();
+  }
+  return RW_OK;
+}
+
+extern "C" rw_status rw_solve_unseeded(const rw_graph* g, const rw_basis* b,
+                                       const float* priors_dev, int32_t K,
+                                       const rw_solve_opts* opts, float* prob_dev,
+                                       uint8_t* labels_dev, const int32_t* disp_dev,
+                                       int32_t disp_dim, float* field_dev, int32_t* m_used,
+                                       void* stream) {
+  if (!g || !b || !priors_dev || !opts || !prob_dev) return RW_ERR_INVALID_ARG;
+  if (b->N != g->N || K < 1 || K > 4096 || (labels_dev && K > 255)) return RW_ERR_INVALID_ARG;
+  if (!(opts->gamma > 0.0)) return opts->gamma == 0.0 ? RW_ERR_UNSUPPORTED : RW_ERR_INVALID_ARG;
+  if (opts->m < 0 || opts->m > b->m || opts->refine_steps < 0 || opts->refine_steps > 100000)
+    return RW_ERR_INVALID_ARG;
+  if (field_dev && (!disp_dev || disp_dim < 1 || disp_dim > 3)) return RW_ERR_INVALID_ARG;
+  if (opts->basis_format != RW_BASIS_F16 && opts->basis_format != RW_BASIS_F32)
+    return RW_ERR_UNSUPPORTED;
+  if (opts->basis_format == RW_BASIS_F32 && b->ld32 > 256) return RW_ERR_UNSUPPORTED;
+  if (g_rw_num_sms <= 0) RW_TRY(rw_device_init());
+  cudaStream_t st = rw_stream(stream);
+  rw_graph* gm = const_cast<rw_graph*>(g);
+  SolveWorkspace& ws = gm->ws;
+  const int64_t N = g->N;
+  const int lp = K <= 4 ? 4 : 8;
+  const int sms = g_rw_num_sms;
+  const int nblk = 4 * sms;
+  const int mq = std::max(b->ld16, b->ld32);
+  // scratch: label array (all unseeded), P-hat and iterate chunks, and the small arrays
+  const size_t cap0 = ws.seedlab.cap;
+  RW_TRY(ws.seedlab.grow(sizeof(int) * N));
+  if (ws.seedlab.cap != cap0) ws.seeds_clean = false;
+  RW_TRY(ws.phat.grow(sizeof(float) * N * lp));
+  RW_TRY(ws.reg.grow(sizeof(float) * N * lp));
+  if (opts->refine_steps > 0) {
+    RW_TRY(ws.xhat[0].grow(sizeof(float) * N * lp));
+    RW_TRY(ws.xhat[1].grow(sizeof(float) * N * lp));
+  }
+  size_t off = 0;
+  auto take = [&](size_t bytes) { size_t r = off; off += (bytes + 255) & ~size_t(255); return r; };
+  const size_t o_mall = take(sizeof(int) * 8), o_mdev = take(sizeof(int) * 8);
+  const size_t o_Z = take(sizeof(float) * mq * lp), o_lgam = take(sizeof(float) * mq);
+  const size_t o_C = take(sizeof(float) * mq * lp), o_Zall = take(sizeof(float) * mq * K);
+  const size_t o_pn = take(sizeof(double) * K), o_g = take(sizeof(double) * K);
+  const size_t o_part = take(sizeof(float) * (size_t)nblk * mq * lp);
+  RW_TRY(ws.small.grow(off));
+  char* base = ws.small.as<char>();
+  int* mall = reinterpret_cast<int*>(base + o_mall);
+  int* mdev = reinterpret_cast<int*>(base + o_mdev);
+  float* Z = reinterpret_cast<float*>(base + o_Z);
+  float* lgam = reinterpret_cast<float*>(base + o_lgam);
+  float* C = reinterpret_cast<float*>(base + o_C);
+  float* Zall = reinterpret_cast<float*>(base + o_Zall);
+  double* pnorm = reinterpret_cast<double*>(base + o_pn);
+  double* gout = reinterpret_cast<double*>(base + o_g);
+  float* part = reinterpret_cast<float*>(base + o_part);
+  if (!ws.seeds_clean)
+    RW_LAUNCH(k_seed_reset, rw_blocks(N, 256), 256, 0, st, ws.seedlab.as<int>(), N, nullptr, 0);
+  ws.seeds_clean = true;   // no seed is placed
+  int proj_per_sm = 2, back_per_sm = 3;
+  launch_shape(N, &proj_per_sm, &back_per_sm);
+  if (opts->basis_format == RW_BASIS_F16) {
+    const float sc = 1.f / b->qscale;
+    RW_TRY(unseeded_passes<__half>(g, b, b->Q16, b->ld16, sc, sc, priors_dev, K, lp, opts,
+                                   prob_dev, st, mall, mdev, Z, lgam, C, Zall, pnorm, gout, part,
+                                   mq, proj_per_sm * sms, back_per_sm * sms));
+  } else {
+    RW_TRY(unseeded_passes<float>(g, b, b->Q32, b->ld32, 1.f, 1.f, priors_dev, K, lp, opts,
+                                  prob_dev, st, mall, mdev, Z, lgam, C, Zall, pnorm, gout, part,
+                                  mq, nblk, nblk));
+  }
+  if (labels_dev || field_dev) {
+    k_reg_finish<<<rw_blocks(N, 256), 256, 0, st>>>(prob_dev, K, N, labels_dev, disp_dev,
+                                                   disp_dim, field_dev);
+    RW_LAUNCH_CHECK();
+  }
+  if (m_used) {
+    int h = 0;
+    RW_CHECK_CUDA(cudaMemcpyAsync(&h, mdev, sizeof(int), cudaMemcpyDeviceToHost, st));
+    RW_CHECK_CUDA(cudaStreamSynchronize(st));
+    *m_used = h;
+    return rw_last_device_status(g, stream);
+  }
+  return RW_OK;
+}
