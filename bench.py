@@ -652,6 +652,38 @@ def registration_block(rw, torch, dev, flush, stream, n=96, m_max=150, reps=20):
     prior_field = disp[np.argmax(P.cpu().numpy(), axis=1)].astype(np.float64)
     epe_prior = float(np.mean(np.linalg.norm(prior_field - truth, axis=1)))
     epe_zero = float(np.mean(np.linalg.norm(truth, axis=1)))
+    # the basic RW with the same priors (PCG, no seeds, label columns in groups of 16) and the
+    # gradient of the squared distance of the expected displacement to the true field with
+    # respect to beta through it (exact path)
+    Ue = torch.empty(N, 27, device=dev)
+    tgt = torch.from_numpy(truth.astype(np.float32)).to(dev)
+    dtorch = torch.from_numpy(disp.astype(np.float32)).to(dev)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    groups = ((0, 16), (16, 27))
+    Ug = []
+    for k0, k1 in groups:
+        Pc = P[:, k0:k1].contiguous()
+        Uc = torch.empty(N, k1 - k0, device=dev)
+        rw.rw_solve_pcg(g, None, None, k1 - k0, Uc, priors=Pc, gamma=1.0, prior_mode=1,
+                        iters=20000, tol=1e-6)
+        Ug.append((Pc, Uc))
+        Ue[:, k0:k1] = Uc
+    torch.cuda.synchronize()
+    exact_s = time.perf_counter() - t0
+    fe = Ue @ dtorch
+    dl_dU = 2.0 * (fe - tgt) @ dtorch.T            # loss = sum_x ||field(x) - truth(x)||^2
+    t0 = time.perf_counter()
+    gbeta = 0.0
+    gw = torch.empty(3 * N, device=dev)
+    for (k0, k1), (Pc, Uc) in zip(groups, Ug):
+        gbeta += rw.rw_grad_exact(g, None, None, k1 - k0, Pc, 1.0, Uc,
+                                  dl_dU[:, k0:k1].contiguous(), gw, rel_tol=1e-6,
+                                  max_iter=20000)
+    torch.cuda.synchronize()
+    grad_s = time.perf_counter() - t0
+    fast_vs_exact = float((prob - Ue).abs().max())
+    epe_exact = float(np.mean(np.linalg.norm(fe.cpu().numpy() - truth, axis=1)))
     rw.rw_basis_free(b)
     rw.rw_graph_free(g)
     return {"workload": "rwir-96x96x96-27labels", "labels": 27, "m_max": m_max,
@@ -659,6 +691,10 @@ def registration_block(rw, torch, dev, flush, stream, n=96, m_max=150, reps=20):
             "priors_ms": pr_ms, "solve_ms": ms - pr_ms,
             "mean_endpoint_error_vox": epe, "mean_endpoint_error_priors_argmax_vox": epe_prior,
             "mean_displacement_magnitude_vox": epe_zero,
+            "fast_vs_exact_maxabs": fast_vs_exact, "mean_endpoint_error_exact_vox": epe_exact,
+            "exact_pcg_s": exact_s,
+            "dloss_dbeta_exact": gbeta, "grad_beta_s": grad_s,
+            "loss": "sum over voxels of ||expected displacement - true displacement||^2",
             "precompute": {"seconds": pre_s, **info},
             "l2": "flushed (256 MB write) before every timed step"}
 

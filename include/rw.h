@@ -261,7 +261,10 @@ rw_status rw_last_device_status(const rw_graph* g, void* stream);
 /* Basic RW on the GPU (the paper's "basic RW", Eq. rw_eq, normalized form of Sec. II-C), by
  * Jacobi-preconditioned CG from a zero start, all labels at once: the comparison solver.
  * Runs exactly `iters` iterations when tol <= 0, else stops when every column's relative
- * residual is <= tol (at most iters).  Same seed/prior/output conventions as rw_solve.
+ * residual is <= tol (at most iters).  Same seed/prior/output conventions as rw_solve, except
+ * that S = 0 is allowed with prior_mode = 1 (registration without landmarks: the seed pointers
+ * may then be NULL); each label column is its own system, so more than RW_MAX_LABELS labels
+ * are solved in groups of columns.
  * *iters_done (host, may be NULL) receives the iterations run; synchronizes if non-NULL. */
 rw_status rw_solve_pcg(const rw_graph* g, const int32_t* seed_idx_dev,
                        const int32_t* seed_lab_dev, int32_t S, int32_t n_labels,
@@ -326,7 +329,9 @@ rw_status rw_update_topology(rw_graph* g, rw_basis* b, const rw_topology_update*
  *                            + lam_b (u_b - p_b))]   (second term only when normalized),
  *   d loss / d beta = sum_e (d loss / d w_e) (d w_e / d beta).
  * U_dev must be the converged exact solution (e.g. rw_solve_pcg with a tight tol) and
- * priors_dev the priors it used (N x n_labels, e.g. from rw_solve_priors).
+ * priors_dev the priors it used (N x n_labels, e.g. from rw_solve_priors).  S = 0 (no seeds,
+ * seed pointers may be NULL) gives the registration gradient; the loss gradients of label
+ * groups add up.
  * grad_w_dev: ndim * N floats in edge-id layout (0 where no edge).  grad_beta_host: 1 double
  * (may be NULL).  Grid graphs only (RW_ERR_UNSUPPORTED for an aggregate's CSR graph); gamma > 0.
  * Returns RW_WARN_NOT_CONVERGED (gradients still written) when the adjoint PCG used max_iter

@@ -206,7 +206,8 @@ def rw_last_device_status(g, stream=None):
 def rw_solve_pcg(g, seed_idx, seed_lab, n_labels, prob, labels=None, priors=None, gamma=1e-3,
                  prior_mode=0, iters=1000, tol=0.0, want_iters=True, stream=None):
     it = C.c_int32(0)
-    _check(abi.lib().rw_solve_pcg(g, _dp(seed_idx), _dp(seed_lab), len(seed_idx), n_labels,
+    S = 0 if seed_idx is None else len(seed_idx)   # no seeds (registration): priors given
+    _check(abi.lib().rw_solve_pcg(g, _dp(seed_idx), _dp(seed_lab), S, n_labels,
                                   _dp(priors), gamma, prior_mode, iters, tol, _dp(prob), _dp(labels),
                                   C.byref(it) if want_iters else None, _stream(stream)),
            "rw_solve_pcg")
@@ -249,7 +250,8 @@ def rw_update_topology(g, b, kind, edge_ids=None, n_bar=0, eta_rowptr=None, eta_
 def rw_grad_exact(g, seed_idx, seed_lab, n_labels, priors, gamma, U, dloss_dU, grad_w,
                   rel_tol=1e-7, max_iter=20000, stream=None):
     gb = C.c_double(0.0)
-    _check(abi.lib().rw_grad_exact(g, _dp(seed_idx), _dp(seed_lab), len(seed_idx), n_labels,
+    S = 0 if seed_idx is None else len(seed_idx)
+    _check(abi.lib().rw_grad_exact(g, _dp(seed_idx), _dp(seed_lab), S, n_labels,
                                    _dp(priors), gamma, _dp(U), _dp(dloss_dU), rel_tol, max_iter,
                                    _dp(grad_w), C.byref(gb), _stream(stream)), "rw_grad_exact")
     return gb.value

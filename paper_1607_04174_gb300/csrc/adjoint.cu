@@ -103,10 +103,9 @@ extern "C" rw_status rw_grad_exact(const rw_graph* g, const int32_t* seed_idx_de
                                    const float* priors_dev, double gamma, const float* U_dev,
                                    const float* dloss_dU_dev, double rel_tol, int32_t max_iter,
                                    float* grad_w_dev, double* grad_beta_host, void* stream) {
-  if (!g || !seed_idx_dev || !seed_lab_dev || !priors_dev || !U_dev || !dloss_dU_dev ||
-      !grad_w_dev)
-    return RW_ERR_INVALID_ARG;
-  if (S < 1 || S > 65536 || n_labels < 1 || n_labels > RW_MAX_LABELS) return RW_ERR_INVALID_ARG;
+  if (!g || !priors_dev || !U_dev || !dloss_dU_dev || !grad_w_dev) return RW_ERR_INVALID_ARG;
+  if (S < 0 || S > 65536 || n_labels < 1 || n_labels > RW_MAX_LABELS) return RW_ERR_INVALID_ARG;
+  if (S > 0 && (!seed_idx_dev || !seed_lab_dev)) return RW_ERR_INVALID_ARG;
   if (!(gamma > 0.0)) return gamma == 0.0 ? RW_ERR_UNSUPPORTED : RW_ERR_INVALID_ARG;
   if (!(rel_tol > 0.0) || max_iter < 1) return RW_ERR_INVALID_ARG;
   if (g->kind != RW_GRAPH_GRID) {

@@ -440,8 +440,10 @@ extern "C" rw_status rw_solve_pcg(const rw_graph* g, const int32_t* seed_idx_dev
                                   const float* priors_dev, double gamma, int32_t prior_mode,
                                   int32_t iters, double tol, float* prob_dev,
                                   uint8_t* labels_dev, int32_t* iters_done, void* stream) {
-  if (!g || !seed_idx_dev || !seed_lab_dev || !prob_dev) return RW_ERR_INVALID_ARG;
-  if (S < 1 || S > 65536 || n_labels < 1 || n_labels > RW_MAX_LABELS) return RW_ERR_INVALID_ARG;
+  if (!g || !prob_dev) return RW_ERR_INVALID_ARG;
+  if (S < 0 || S > 65536 || n_labels < 1 || n_labels > RW_MAX_LABELS) return RW_ERR_INVALID_ARG;
+  if (S > 0 && (!seed_idx_dev || !seed_lab_dev)) return RW_ERR_INVALID_ARG;
+  if (S == 0 && prior_mode != 1) return RW_ERR_INVALID_ARG;   // no seeds: priors are given
   if (!(gamma > 0.0)) return gamma == 0.0 ? RW_ERR_UNSUPPORTED : RW_ERR_INVALID_ARG;
   if (iters < 0 || (prior_mode == 1 && !priors_dev) || (prior_mode == 0 && !g->J))
     return RW_ERR_INVALID_ARG;

@@ -2842,7 +2842,8 @@ rw_status rw_solve_priors_internal(const rw_graph* g, const int32_t* seed_idx,
                                    int** seedlab_out, double** fit64_out, bool defer_priors) {
   rw_graph* gm = const_cast<rw_graph*>(g);
   SolveWorkspace& ws = gm->ws;
-  if (S > kMaxSeeds) return RW_ERR_INVALID_ARG;
+  if (S > kMaxSeeds || S < 0) return RW_ERR_INVALID_ARG;
+  if (S == 0 && prior_mode != 1) return RW_ERR_INVALID_ARG;   // no seeds: priors are given
   const size_t cap0 = ws.seedlab.cap;
   RW_TRY(ws.seedlab.grow(sizeof(int) * g->N));
   if (ws.seedlab.cap != cap0) ws.seeds_clean = false;
@@ -2857,10 +2858,11 @@ rw_status rw_solve_priors_internal(const rw_graph* g, const int32_t* seed_idx,
   // seeds (rw_solve does); otherwise reset it here
   if (!ws.seeds_clean)
     RW_LAUNCH(k_seed_reset, rw_blocks(g->N, 256), 256, 0, st, seedlab, g->N, nullptr, 0);
-  ws.seeds_clean = false;
+  ws.seeds_clean = S == 0;   // nothing scattered: the label array stays all -1
   ws.seed_nsb = nsb;
-  RW_LAUNCH(k_seed_scatter, nsb, 256, 0, st, seed_idx, seed_lab, S, L, g->N,
-            g->J ? g->J : nullptr, seedlab, bpart, g->status);
+  if (S > 0)
+    RW_LAUNCH(k_seed_scatter, nsb, 256, 0, st, seed_idx, seed_lab, S, L, g->N,
+              g->J ? g->J : nullptr, seedlab, bpart, g->status);
   if (!defer_priors) RW_TRY(launch_priors(g, L, prior_mode, priors, lp, 0, st));
   *phat_out = ws.phat.as<float>();
   *seedlab_out = seedlab;

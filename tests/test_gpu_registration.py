@@ -93,3 +93,43 @@ def test_unseeded_solve_matches_oracle(case3d, m, fmt):
     finally:
         rw.rw_basis_free(b)
         rw.rw_graph_free(g)
+
+
+def test_unseeded_exact_solve_and_beta_gradient(case3d):
+    """The basic RW with priors and no seeds (rw_solve_pcg, S = 0) and the exact-path gradient
+    (rw_grad_exact, S = 0) against the oracle's FP64 solve and adjoint, 27 labels in two groups
+    of columns (16 + 11)."""
+    from oracle import adjoint, exact
+    c = case3d
+    go = c["go"]
+    N = go.N
+    P64 = f32(c["P"])
+    none = np.zeros(0, np.int64)
+    Ue = exact.exact_rw(go, none, none, 27, P64, GAMMA)
+    G = np.random.default_rng(5).standard_normal((N, 27))
+    gw_o, gb_o = adjoint.exact_grad(go, none, none, 27, P64, GAMMA, G, U=Ue)
+    g = rw.rw_build_graph(to_dev(c["F"], torch.float32), c["dims"], BETA)
+    try:
+        U = np.zeros((N, 27))
+        gw = np.zeros(3 * N)
+        gb = 0.0
+        for k0, k1 in ((0, 16), (16, 27)):
+            Pc = to_dev(np.ascontiguousarray(P64[:, k0:k1]), torch.float32)
+            Uc = torch.empty(N, k1 - k0, device=dev())
+            rw.rw_solve_pcg(g, None, None, k1 - k0, Uc, priors=Pc, gamma=GAMMA, prior_mode=1,
+                            iters=20000, tol=1e-7)
+            U[:, k0:k1] = Uc.cpu().numpy()
+            gwc = torch.empty(3 * N, device=dev())
+            gb += rw.rw_grad_exact(g, None, None, k1 - k0, Pc, GAMMA, Uc,
+                                   to_dev(np.ascontiguousarray(G[:, k0:k1]), torch.float32), gwc,
+                                   rel_tol=1e-7, max_iter=20000)
+            gw += gwc.cpu().numpy()
+        assert np.abs(U - Ue).max() <= 1e-4
+        by_id = np.zeros(3 * N)
+        by_id[go.ids] = gw_o
+        scale = np.abs(by_id).max()
+        assert np.abs(gw - by_id).max() <= 1e-3 * scale
+        print(f"registration d loss/d beta: GPU {gb:.6e}, oracle {gb_o:.6e}")
+        assert abs(gb - gb_o) <= 1e-3 * abs(gb_o)
+    finally:
+        rw.rw_graph_free(g)
