@@ -460,6 +460,12 @@ rw_status rw_solve_unseeded(const rw_graph* g, const rw_basis* b, const float* p
                             uint8_t* labels_dev, const int32_t* disp_dev, int32_t disp_dim,
                             float* field_dev, int32_t* m_used, void* stream);
 
+/* Several bases precomputed at betas_host[0..n-1] (Sec. III-B, last paragraph: Eq. z_ray
+ * "interpolates" between them): the index of the one to update for `beta`, the nearest in log
+ * beta (ties to the lower index); -1 when n < 1 or a beta is not positive.  Host only; the
+ * caller then applies rw_update_weights(RW_UPDATE_BETA, beta) to that basis. */
+int32_t rw_basis_nearest_beta(const double* betas_host, int32_t n, double beta);
+
 /* Writes the Gaussian-fit priors of Sec. IV-A (N x n_labels, node-major) for the seeds. */
 rw_status rw_solve_priors(const rw_graph* g, const int32_t* seed_idx_dev,
                           const int32_t* seed_lab_dev, int32_t S, int32_t n_labels,

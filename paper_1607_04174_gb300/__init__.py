@@ -419,3 +419,10 @@ def rw_solve_unseeded(g, b, priors, prob, labels=None, disp=None, field=None, ga
                                        C.byref(mu) if want_m else None, _stream(stream)),
            "rw_solve_unseeded")
     return mu.value if want_m else None
+
+
+def rw_basis_nearest_beta(betas, beta):
+    """Index of the precomputed beta' nearest to beta in log beta (-1 if invalid)."""
+    arr = np.ascontiguousarray(betas, dtype=np.float64)
+    return abi.lib().rw_basis_nearest_beta(arr.ctypes.data_as(C.POINTER(C.c_double)), len(arr),
+                                           float(beta))

@@ -640,3 +640,21 @@ extern "C" rw_status rw_rayleigh_quotients_noalloc(const rw_graph* g, const floa
   RW_LAUNCH_CHECK();
   return RW_OK;
 }
+
+// ---------------------------------------------------------------------------------------
+// Several precomputed bases (Sec. III-B, last paragraph: eigenvectors precomputed for several
+// beta' and Eq. z_ray used to "interpolate" between them): the basis to update for a new beta
+// is the one whose beta' is nearest in log beta (doubling beta squares the weights of the
+// squared form, so distances between betas are ratios); ties go to the lower index.
+// ---------------------------------------------------------------------------------------
+extern "C" int32_t rw_basis_nearest_beta(const double* betas_host, int32_t n, double beta) {
+  if (!betas_host || n < 1 || !(beta > 0.0)) return -1;
+  int best = -1;
+  double bd = 0.0;
+  for (int k = 0; k < n; ++k) {
+    if (!(betas_host[k] > 0.0)) return -1;
+    const double d = fabs(log(betas_host[k]) - log(beta));
+    if (best < 0 || d < bd) { best = k; bd = d; }
+  }
+  return best;
+}

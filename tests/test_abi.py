@@ -104,7 +104,8 @@ def test_null_handles_are_refused_on_the_host(lib):
     from paper_1607_04174_gb300 import abi
     before = lib.rw_kernel_launches()
     status_calls = [n for n, (res, _) in abi.PROTOTYPES.items()
-                    if res is C.c_int32 and n not in ("rw_basis_m", "rw_set_launch_shape")]
+                    if res is C.c_int32 and n not in ("rw_basis_m", "rw_set_launch_shape",
+                                                      "rw_basis_nearest_beta")]
     assert len(status_calls) >= 17
     for name in status_calls:
         st = getattr(lib, name)(*_null_args(abi.PROTOTYPES[name][1]))
@@ -115,6 +116,7 @@ def test_null_handles_are_refused_on_the_host(lib):
     assert lib.rw_set_launch_shape(4096, 0, 3) == -1      # a shape out of range
     assert lib.rw_set_launch_shape(4096, 1, 9) == -1
     assert lib.rw_set_launch_shape(0, 1, 1) == 0          # clears the (host-side) table
+    assert lib.rw_basis_nearest_beta(None, 1, 1.0) == -1
     lib.rw_batch_free(None)
     assert lib.rw_block_gram_scratch_bytes(2048, 128, 256) == 256 + 4 * 128 * 256 * 2
     lib.rw_graph_free(None)
@@ -123,6 +125,7 @@ def test_null_handles_are_refused_on_the_host(lib):
     # every declared entry point is one of the calls above or an accessor checked elsewhere
     covered = set(status_calls) | {"rw_basis_m", "rw_graph_num_nodes", "rw_graph_free",
                                    "rw_block_gram_scratch_bytes", "rw_set_launch_shape",
+                                   "rw_basis_nearest_beta",
                                    "rw_batch_free",
                                    "rw_basis_free", "rw_status_str", "rw_last_error_message",
                                    "rw_kernel_launches"}
@@ -202,3 +205,20 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
         rw.rw_kernel_launches()
     with pytest.raises(ImportError, match="missing"):
         rw.rw_status_str(0)
+
+
+def test_nearest_beta_in_log_space(lib):
+    """Host-only selection among bases precomputed at several beta' (Sec. III-B): nearest in
+    log beta, ties to the lower index, invalid input refused."""
+    import numpy as np
+    import paper_1607_04174_gb300 as rw
+    betas = [45.0, 90.0, 180.0]
+    assert rw.rw_basis_nearest_beta(betas, 150.0) == 2      # |log 150/180| < |log 150/90|
+    assert rw.rw_basis_nearest_beta(betas, 120.0) == 1      # |log 120/90| < |log 120/180|
+    assert rw.rw_basis_nearest_beta(betas, 10.0) == 0
+    assert rw.rw_basis_nearest_beta([40.0, 160.0], 80.0) == 0   # equal ratios: lower index
+    assert rw.rw_basis_nearest_beta(betas, 0.0) == -1
+    assert rw.rw_basis_nearest_beta([1.0, -2.0], 1.0) == -1
+    for beta in np.geomspace(5.0, 500.0, 23):
+        want = int(np.argmin(np.abs(np.log(betas) - np.log(beta))))
+        assert rw.rw_basis_nearest_beta(betas, beta) == want

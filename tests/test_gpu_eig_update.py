@@ -146,3 +146,43 @@ def test_edge_list_update_and_removal():
     finally:
         rw.rw_basis_free(b)
         rw.rw_graph_free(g)
+
+
+def test_multi_beta_bases_select_and_update():
+    """Bases precomputed at beta' = 45, 90, 180 (Sec. III-B, last paragraph): for beta = 150
+    the nearest in log beta (180) is chosen and updated by Eq. (z_ray); its values equal the
+    oracle's Rayleigh quotients of that basis under beta = 150.  The distance of each choice's
+    solve from the exact solve at beta = 150 is printed, not asserted (the paper compares such
+    approximations only through segmentation quality)."""
+    from oracle import exact, fastrw, priors
+    case = c1_case(size=40, per=8, m=40)
+    J, dims = case["J"], case["dims"]
+    betas = [45.0, 90.0, 180.0]
+    k = rw.rw_basis_nearest_beta(betas, 150.0)
+    assert k == 2
+    g150 = graph.build_graph(J, dims, 150.0)
+    P = priors.gaussian_priors(J, case["si"], case["sl"], 2)
+    Ue = exact.exact_rw(g150, case["si"], case["sl"], 2, P, 1e-3)
+    errs = []
+    for j, bp in enumerate(betas):
+        go = graph.build_graph(J, dims, bp)
+        lam, Q = eig.smallest_eigpairs(go.Lhat, 40)
+        Q = f32(Q)
+        g = rw.rw_build_graph(to_dev(J, torch.float32), dims, bp)
+        b = rw.rw_basis_create(g, to_dev(Q, torch.float32), lam)
+        try:
+            rw.rw_update_weights(g, b, rw.RW_UPDATE_BETA, beta=150.0)
+            got = rw.rw_basis_get(b)
+            ref = update.updated_values(update.update_beta(go, 150.0), Q)
+            np.testing.assert_allclose(got, ref, rtol=2e-5, atol=1e-9)
+            prob = torch.empty(go.N, 2, device=dev())
+            rw.rw_solve(g, b, to_dev(case["si"]), to_dev(case["sl"]), 2, prob, m=40,
+                        refine_steps=0, basis_format=rw.RW_BASIS_F32, want_info=False)
+            errs.append(float(np.abs(prob.cpu().numpy() - Ue).max()))
+            if j == k:   # the chosen basis: GPU solve = oracle fast RW on the updated values
+                Uf = fastrw.fast_rw(g150, Q, ref, case["si"], case["sl"], 2, P, 1e-3)
+                assert np.abs(prob.cpu().numpy() - Uf).max() <= 1e-3
+        finally:
+            rw.rw_basis_free(b)
+            rw.rw_graph_free(g)
+    print("max |U - U_exact(beta=150)| from beta' = 45, 90, 180:", errs)
