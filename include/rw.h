@@ -440,7 +440,8 @@ rw_status rw_set_launch_shape(int64_t n_max, int32_t proj_per_sm, int32_t back_p
  * of absolute differences between fixed(x + o) and moving(x + o + d_k) over the patch offsets
  * o in [-half, half]^ndim (coordinates clamped into the grid), squared, negated, exponentiated
  * and normalized to sum to 1 over the labels at each voxel.  dims[0..ndim-1] as for graphs;
- * 1 <= K <= 4096, 0 <= half <= 8.  Asynchronous.
+ * 1 <= K <= 4096, 0 <= half <= 8.  Asynchronous; two intermediate volumes of
+ * (dims + 2 half) x K floats are allocated and freed in stream order (cudaMallocAsync).
  * rw_solve_unseeded: the fast RW with priors and no seeds, Eq. (U_lin_comb) with S = 0:
  * U-hat = Q Lambda_gamma (gamma Q^T P-hat), then opts->refine_steps damped-Jacobi steps of
  * Eq. (rw_eq) (no seeded rows).  opts->m = 0 chooses m by Eq. (g): the first candidate
