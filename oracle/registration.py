@@ -41,13 +41,16 @@ def _clamped(a, dims):
     return np.clip(a, 0, np.asarray(dims)[None, :] - 1)
 
 
-def patch_sad(I_f, I_m, dims, disp, half=2):
-    """SAD_k(x) over the (2 half + 1)^d patch, N x K.  I_f, I_m: flat arrays (x fastest)."""
+def patch_sad(I_f, I_m, dims, disp, half=2, voxels=None):
+    """SAD_k(x) over the (2 half + 1)^d patch, N x K (or len(voxels) x K for the listed flat
+    voxel indices only).  I_f, I_m: flat arrays (x fastest)."""
     dims = tuple(int(k) for k in dims)
-    N = int(np.prod(dims))
     F = np.asarray(I_f, dtype=np.float64).reshape(tuple(reversed(dims)))
     M = np.asarray(I_m, dtype=np.float64).reshape(tuple(reversed(dims)))
     idx = np.indices(tuple(reversed(dims))).reshape(len(dims), -1)[::-1].T   # (x, y, z) rows
+    if voxels is not None:
+        idx = idx[np.asarray(voxels)]
+    N = idx.shape[0]
     out = np.zeros((N, len(disp)))
     offs = np.stack(np.meshgrid(*([np.arange(-half, half + 1)] * len(dims)), indexing="ij"),
                     axis=-1).reshape(-1, len(dims))
@@ -63,8 +66,8 @@ def patch_sad(I_f, I_m, dims, disp, half=2):
     return out
 
 
-def registration_priors(I_f, I_m, dims, disp, half=2):
-    s = patch_sad(I_f, I_m, dims, disp, half)
+def registration_priors(I_f, I_m, dims, disp, half=2, voxels=None):
+    s = patch_sad(I_f, I_m, dims, disp, half, voxels)
     logp = -s * s
     logp -= logp.max(axis=1, keepdims=True)
     P = np.exp(logp)

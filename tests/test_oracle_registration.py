@@ -84,3 +84,14 @@ def test_unseeded_fast_solve_is_exact_at_full_rank():
     np.testing.assert_allclose(Ue.sum(axis=1), 1.0, atol=1e-10)
     field = registration.expected_displacement(np.eye(27)[[13, 0]], disp)
     np.testing.assert_array_equal(field, [[0, 0, 0], [-1, -1, -1]])
+
+
+def test_patch_sad_on_a_voxel_subset_equals_the_full_map():
+    dims = (7, 6, 5)
+    rng = np.random.default_rng(3)
+    F, M = rng.random(210), rng.random(210)
+    disp = registration.displacement_labels()
+    full = registration.registration_priors(F, M, dims, disp, half=2)
+    vox = np.array([0, 17, 104, 209])
+    np.testing.assert_array_equal(registration.registration_priors(F, M, dims, disp, half=2,
+                                                                   voxels=vox), full[vox])
