@@ -213,55 +213,65 @@ k_stencil_wide(const float* __restrict__ X, int64_t ldx, float* __restrict__ Y, 
   }
 }
 
-// Grid graphs, the bandwidth-bound default: one thread per (voxel, float4 chunk of its row).
-// Threads of a row of voxels are consecutive (chunk fastest), so a warp reads 512 contiguous
-// bytes of X per access and every thread issues its own row and all 2 ndim neighbour rows at
-// once (the x neighbours hit L1, the y and z neighbours L2).  y and z come from the block
-// index; one division by the chunk count per thread.
+// Grid graphs, the bandwidth-bound default: one thread per (x, float4 chunk) column of a
+// segment of RY consecutive rows along y.  Threads of a row of voxels are consecutive (chunk
+// fastest), so a warp reads 512 contiguous bytes of X per access.  The thread marches along y
+// keeping rows y - 1, y, y + 1 in registers and loading two rows ahead, so per output it reads
+// one new row (the first touch from DRAM) plus the x neighbours (L1: the neighbouring threads'
+// rows) and the z neighbours (L2); the earlier one-output-per-thread form also read both y
+// neighbours from L2 and was 11-33% slower.
+template <int RY>
 __global__ void __launch_bounds__(256)
-k_stencil_flat(const float* __restrict__ X, int64_t ldx, float* __restrict__ Y, int64_t ldy,
-               int nch, const float* __restrict__ cw, const float* __restrict__ dg,
-               int normalized, int ndim, int DX, int DY, int DZ, int64_t N, float alpha,
-               float beta, const float* __restrict__ Zm, int64_t ldz, float gamma) {
+k_stencil_yroll(const float* __restrict__ X, int64_t ldx, float* __restrict__ Y, int64_t ldy,
+                int nch, const float* __restrict__ cw, const float* __restrict__ dg,
+                int normalized, int ndim, int DX, int DY, int DZ, int64_t N, float alpha,
+                float beta, const float* __restrict__ Zm, int64_t ldz, float gamma) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= DX * nch) return;
   const int x = t / nch, c = t - x * nch;
-  const int y = blockIdx.y, z = blockIdx.z;
+  const int y0 = blockIdx.y * RY, y1 = min(DY, y0 + RY), z = blockIdx.z;
   const int64_t sy = DX, sz = (int64_t)DX * DY;
-  const int64_t i = x + sy * y + sz * z;
-  auto ld = [&](int64_t j) { return __ldg(reinterpret_cast<const float4*>(X + j * ldx) + c); };
   const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
-  // every load first: own row, the neighbours, their coefficients
-  const float4 xo = ld(i);
-  const bool hx0 = x > 0, hx1 = x + 1 < DX, hy0 = y > 0, hy1 = y + 1 < DY;
+  auto ld = [&](int64_t j) { return __ldg(reinterpret_cast<const float4*>(X + j * ldx) + c); };
+  const int64_t ib = x + sz * z;
+  float4 prv = y0 > 0 ? ld(ib + sy * (y0 - 1)) : zero;
+  float4 cur = ld(ib + sy * y0);
+  float4 nx1 = y0 + 1 < DY ? ld(ib + sy * (y0 + 1)) : zero;
+  float4 nx2 = y0 + 2 < DY ? ld(ib + sy * (y0 + 2)) : zero;
+  const bool hx0 = x > 0, hx1 = x + 1 < DX;
   const bool hz0 = ndim == 3 && z > 0, hz1 = ndim == 3 && z + 1 < DZ;
-  const float4 vx0 = hx0 ? ld(i - 1) : zero, vx1 = hx1 ? ld(i + 1) : zero;
-  const float4 vy0 = hy0 ? ld(i - sy) : zero, vy1 = hy1 ? ld(i + sy) : zero;
-  const float4 vz0 = hz0 ? ld(i - sz) : zero, vz1 = hz1 ? ld(i + sz) : zero;
-  const float cx0 = hx0 ? __ldg(cw + i - 1) : 0.f, cx1 = hx1 ? __ldg(cw + i) : 0.f;
-  const float cy0 = hy0 ? __ldg(cw + N + i - sy) : 0.f, cy1 = hy1 ? __ldg(cw + N + i) : 0.f;
-  const float cz0 = hz0 ? __ldg(cw + 2 * N + i - sz) : 0.f;
-  const float cz1 = hz1 ? __ldg(cw + 2 * N + i) : 0.f;
-  const float dd = normalized ? 1.f : __ldg(dg + i);
-  float4 zz = zero;
-  if (Zm) zz = __ldg(reinterpret_cast<const float4*>(Zm + i * ldz) + c);
-  auto lap = [&](float o, float a0, float a1, float b0, float b1, float e0, float e1) {
-    float acc = dd * o;
-    acc = fmaf(-cx0, a0, acc); acc = fmaf(-cx1, a1, acc);
-    acc = fmaf(-cy0, b0, acc); acc = fmaf(-cy1, b1, acc);
-    acc = fmaf(-cz0, e0, acc); acc = fmaf(-cz1, e1, acc);
-    return alpha * acc + beta * o;
-  };
-  float4 out;
-  out.x = lap(xo.x, vx0.x, vx1.x, vy0.x, vy1.x, vz0.x, vz1.x);
-  out.y = lap(xo.y, vx0.y, vx1.y, vy0.y, vy1.y, vz0.y, vz1.y);
-  out.z = lap(xo.z, vx0.z, vx1.z, vy0.z, vy1.z, vz0.z, vz1.z);
-  out.w = lap(xo.w, vx0.w, vx1.w, vy0.w, vy1.w, vz0.w, vz1.w);
-  if (Zm) {
-    out.x = fmaf(gamma, zz.x, out.x); out.y = fmaf(gamma, zz.y, out.y);
-    out.z = fmaf(gamma, zz.z, out.z); out.w = fmaf(gamma, zz.w, out.w);
+  for (int y = y0; y < y1; ++y) {
+    const int64_t i = ib + sy * y;
+    const float4 vx0 = hx0 ? ld(i - 1) : zero, vx1 = hx1 ? ld(i + 1) : zero;
+    const float4 vz0 = hz0 ? ld(i - sz) : zero, vz1 = hz1 ? ld(i + sz) : zero;
+    // two rows ahead (the window's last row is y1, the segment's lower neighbour)
+    const float4 nx3 = (y + 3 < DY && y + 3 <= y1) ? ld(i + 3 * sy) : zero;
+    const float cx0 = hx0 ? __ldg(cw + i - 1) : 0.f, cx1 = hx1 ? __ldg(cw + i) : 0.f;
+    const float cy0 = y > 0 ? __ldg(cw + N + i - sy) : 0.f;
+    const float cy1 = y + 1 < DY ? __ldg(cw + N + i) : 0.f;
+    const float cz0 = hz0 ? __ldg(cw + 2 * N + i - sz) : 0.f;
+    const float cz1 = hz1 ? __ldg(cw + 2 * N + i) : 0.f;
+    const float dd = normalized ? 1.f : __ldg(dg + i);
+    auto lap = [&](float o, float a0, float a1, float b0, float b1, float e0, float e1) {
+      float acc = dd * o;
+      acc = fmaf(-cx0, a0, acc); acc = fmaf(-cx1, a1, acc);
+      acc = fmaf(-cy0, b0, acc); acc = fmaf(-cy1, b1, acc);
+      acc = fmaf(-cz0, e0, acc); acc = fmaf(-cz1, e1, acc);
+      return alpha * acc + beta * o;
+    };
+    float4 out;
+    out.x = lap(cur.x, vx0.x, vx1.x, prv.x, nx1.x, vz0.x, vz1.x);
+    out.y = lap(cur.y, vx0.y, vx1.y, prv.y, nx1.y, vz0.y, vz1.y);
+    out.z = lap(cur.z, vx0.z, vx1.z, prv.z, nx1.z, vz0.z, vz1.z);
+    out.w = lap(cur.w, vx0.w, vx1.w, prv.w, nx1.w, vz0.w, vz1.w);
+    if (Zm) {
+      const float4 zz = __ldg(reinterpret_cast<const float4*>(Zm + i * ldz) + c);
+      out.x = fmaf(gamma, zz.x, out.x); out.y = fmaf(gamma, zz.y, out.y);
+      out.z = fmaf(gamma, zz.z, out.z); out.w = fmaf(gamma, zz.w, out.w);
+    }
+    reinterpret_cast<float4*>(Y + i * ldy)[c] = out;
+    prv = cur; cur = nx1; nx1 = nx2; nx2 = nx3;
   }
-  reinterpret_cast<float4*>(Y + i * ldy)[c] = out;
 }
 
 // general (CSR) graph: one warp per row
@@ -330,12 +340,19 @@ rw_status rw_stencil_apply(const rw_graph* g, const float* X, int64_t ldx, float
   if (k <= 0 || k > 1024) return RW_ERR_INVALID_ARG;
   const int nch = (k + 3) / 4;
   if (g->kind == RW_GRAPH_GRID && (int64_t)g->dims[0] * nch < ((int64_t)1 << 31) &&
-      g->dims[1] <= 65535 && g->dims[2] <= 65535) {
-    const dim3 grid(rw_blocks((int64_t)g->dims[0] * nch, 256), (unsigned)g->dims[1],
-                    (unsigned)g->dims[2]);
-    k_stencil_flat<<<grid, 256, 0, st>>>(X, ldx, Y, ldy, nch, g->cw, g->d, g->normalized,
-                                        g->ndim, g->dims[0], g->dims[1], g->dims[2], g->N,
-                                        alpha, beta, Z, ldz, gamma);
+      g->dims[2] <= 65535) {
+    // segments of 8 rows (2-D) / 16 rows (3-D): the fastest in a sweep on GB300
+    const int ry = g->ndim == 3 ? 16 : 8;
+    const dim3 grid(rw_blocks((int64_t)g->dims[0] * nch, 256),
+                    (unsigned)((g->dims[1] + ry - 1) / ry), (unsigned)g->dims[2]);
+    if (ry == 16)
+      k_stencil_yroll<16><<<grid, 256, 0, st>>>(X, ldx, Y, ldy, nch, g->cw, g->d, g->normalized,
+                                                 g->ndim, g->dims[0], g->dims[1], g->dims[2],
+                                                 g->N, alpha, beta, Z, ldz, gamma);
+    else
+      k_stencil_yroll<8><<<grid, 256, 0, st>>>(X, ldx, Y, ldy, nch, g->cw, g->d, g->normalized,
+                                                g->ndim, g->dims[0], g->dims[1], g->dims[2],
+                                                g->N, alpha, beta, Z, ldz, gamma);
     RW_LAUNCH_CHECK();
     return RW_OK;
   }
