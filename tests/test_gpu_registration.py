@@ -133,3 +133,28 @@ def test_unseeded_exact_solve_and_beta_gradient(case3d):
         assert abs(gb - gb_o) <= 1e-3 * abs(gb_o)
     finally:
         rw.rw_graph_free(g)
+
+
+def test_unseeded_solve_few_labels_2d():
+    """K = 3 labels (chunks of 4 padded columns) on a 2-D graph, fixed m, no refinement (the
+    back-projection writes U directly)."""
+    dims = (30, 26)
+    F = f32(synth.smooth_random_image(dims, seed=14, smooth=2.0, sigma=0.02))
+    go = graph.build_graph(F, dims, BETA)
+    lam, Q = eig.smallest_eigpairs(go.Lhat, 50)
+    Q = f32(Q)
+    rng = np.random.default_rng(15)
+    P = rng.random((go.N, 3)) + 0.2
+    P = f32(P / P.sum(axis=1, keepdims=True))
+    g = rw.rw_build_graph(to_dev(F, torch.float32), dims, BETA)
+    b = rw.rw_basis_create(g, to_dev(Q, torch.float32), lam)
+    try:
+        prob = torch.empty(go.N, 3, device=dev())
+        m_used = rw.rw_solve_unseeded(g, b, to_dev(P, torch.float32), prob, gamma=0.5, m=30,
+                                      refine_steps=0)
+        assert m_used == 30
+        ref = registration.registration_solve(go, Q, lam, P, gamma=0.5, m=30, refine_steps=0)
+        assert np.abs(prob.cpu().numpy() - ref["U"]).max() <= TOL_PROB
+    finally:
+        rw.rw_basis_free(b)
+        rw.rw_graph_free(g)
