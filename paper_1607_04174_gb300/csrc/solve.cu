@@ -1315,7 +1315,13 @@ __device__ void adapt_body(const float* __restrict__ G, int ldg, const float* __
   for (int k = 0; k < L; ++k)
     if (!(nk[k] <= (float)rho)) inside = false;
   if (!inside) {
-    // trust region for candidates c, c + 1, ... (rare: the fit leaves the ball)
+    // trust region for candidates c, c + 1, ... (the fit leaves the ball: few seeds, m > S).
+    // Each label's Newton starts from the mu it reached on the previous candidate (the
+    // constrained solution's mu grows with m, so the warm start stays on the left of the root,
+    // where the iteration is monotone).
+    __shared__ float s_muw[RW_MAX_LABELS];
+    if (tid < RW_MAX_LABELS) s_muw[tid] = 0.f;
+    __syncthreads();
     (void)rows_done;
     for (; c < ncand; ++c) {
       m = cand_m(c);
@@ -1337,12 +1343,30 @@ __device__ void adapt_body(const float* __restrict__ G, int ldg, const float* __
         if (lane == 0) nk[k] = sqrtf(s2);
       }
       __syncthreads();
+      bool refactored = false;   // B2 still holds the factor of G_m + mu0 I
       for (int k = 0; k < L && okc; ++k) {
         if (!(nk[k] > (float)rho)) continue;
         // Newton from the left converges quadratically; in FP32 an ill-conditioned G_m + mu I
         // can keep ||a|| from settling below 1e-5 rho, so stop at 1e-4 rho or after 12 steps
         // (each step refactors the m x m matrix on one CTA; 40 steps cost milliseconds)
-        float mu = mu0;
+        float mu = fmaxf(mu0, s_muw[k]);
+        if (mu > mu0 || refactored) {   // factor and solve at this label's starting mu
+          __syncthreads();
+          load_shifted_gram(B2, m, mss, G, ldg, mu);
+          __syncthreads();
+          if (!chol_lower_smem(B2, m, mss)) { okc = false; break; }
+          if (warp == 0) {
+            for (int i = lane; i < m; i += 32) z[k * mmax + i] = bv[(int64_t)i * ldb + k];
+            __syncwarp();
+            fwd_lower_warp(B2, m, mss, z + k * mmax, z + k * mmax);
+            bwd_lowerT_warp(B2, m, mss, z + k * mmax, al + k * mmax);
+            float s2 = 0.f;
+            for (int i = lane; i < m; i += 32) s2 = fmaf(al[k * mmax + i], al[k * mmax + i], s2);
+            s2 = warp_sum(s2);
+            if (lane == 0) nk[k] = sqrtf(s2);
+          }
+        }
+        refactored = true;
         for (int it = 0; it < 12; ++it) {
           __syncthreads();
           const float na = nk[k];
@@ -1371,7 +1395,9 @@ __device__ void adapt_body(const float* __restrict__ G, int ldg, const float* __
           }
         }
         __syncthreads();
+        if (tid == 0) s_muw[k] = mu;   // the next candidate's start for this label
       }
+      __syncthreads();
       seed_residuals(Qs, ldq, Us, ldu, S, L, m, al, fk, mmax);
       bool pass = okc;
       for (int k = 0; k < L; ++k)
