@@ -497,6 +497,45 @@ def beta_update_block(rw, torch, dev, g, b, J32, dims, truth, flush, stream, n_s
             "reference": "basic RW at beta = 150 by PCG to a relative residual of 1e-7"}
 
 
+def gamma0_block(rw, torch, dev, g, b, dims, truth, flush, stream, n_sets=4):
+    """gamma = 0 (no priors; Sec. II-B, after Eq. Fs: the null vector of L-hat replaces basis
+    column 0 and the column sums enter the seeded system) on the 512^2 workload's graph and
+    LOBPCG basis: adaptive m with 3 refinement steps, and m = 200 without refinement, each
+    against the converged basic RW at gamma = 0 (L_n U_n = -B^T U_s by PCG to 1e-7)."""
+    N = int(np.prod(dims))
+    sets = seed_sets(truth, dims, n_sets, synth.BASE_SEED + 9101)
+    dsets = [(torch.from_numpy(si).to(dev), torch.from_numpy(sl).to(dev)) for si, sl in sets]
+    prob = torch.empty(N, LABELS, device=dev)
+    lab = torch.empty(N, dtype=torch.uint8, device=dev)
+    conv = torch.empty(N, LABELS, device=dev)
+    lab_ex = torch.empty(N, dtype=torch.uint8, device=dev)
+    modes = {"adaptive_refine3": dict(gamma=0.0, m=0, m_step=M_STEP, eps=EPS, refine_steps=REFINE),
+             "m200_no_refine": dict(gamma=0.0, m=M, refine_steps=0)}
+    rows = {k: [] for k in modes}
+    iters = []
+    for si, sl in dsets:
+        iters.append(rw.rw_solve_pcg(g, si, sl, LABELS, conv, lab_ex, gamma=0.0, iters=50000,
+                                     tol=1e-7))
+        for tag, kw in modes.items():
+            _, inf = rw.rw_solve(g, b, si, sl, LABELS, prob, lab, **kw)
+            rows[tag].append({"maxabs": float((prob - conv).abs().max()),
+                              "label_agreement": float((lab == lab_ex).float().mean()),
+                              "m_used": inf["m_used"]})
+    out = {"seed_sets": n_sets, "pcg_iters_converged_1e-7_mean": float(np.mean(iters)),
+           "reference": "basic RW at gamma = 0 by PCG to a relative residual of 1e-7"}
+    for tag, kw in modes.items():
+        r = rows[tag]
+        ms = time_steps(lambda k: rw.rw_solve(g, b, dsets[k % n_sets][0], dsets[k % n_sets][1],
+                                              LABELS, prob, lab, want_info=False, **kw),
+                        20, flush, stream)
+        out[tag] = {"maxabs_vs_exact_mean": float(np.mean([x["maxabs"] for x in r])),
+                    "maxabs_vs_exact_max": float(np.max([x["maxabs"] for x in r])),
+                    "label_agreement_mean": float(np.mean([x["label_agreement"] for x in r])),
+                    "m_used_mean": float(np.mean([x["m_used"] for x in r])),
+                    "solve_ms": ms, "label_maps_per_s": 1000.0 / ms}
+    return out
+
+
 BATCH_IMAGES, BATCH_ROUNDS, BATCH_M, BATCH_TOL, BATCH_STREAMS = 64, 8, 100, 1e-4, 8
 
 
@@ -960,6 +999,8 @@ def gpu_arm(args):
                          f"same seed sets as the GPU phase pass",
                "same_config": True,
                "adaptive_m_agreement": f"{agree}/{len(m_or)}"}
+    gamma0 = None if args.no_gamma0 else gamma0_block(rw, torch, dev, g, b, dims, truth, flush,
+                                                         stream)
     batched = None if args.no_batch else batch_block(rw, torch, dev)
     regist = None if args.no_registration else registration_block(rw, torch, dev, flush, stream)
     beta_upd = None if args.no_beta_update else beta_update_block(
@@ -995,6 +1036,7 @@ def gpu_arm(args):
         "c3_128cubed": c3,
         "stencil": stencil,
         "beta_update_512": beta_upd,
+        "gamma0_512": gamma0,
         "batched_c4": batched,
         "registration_c5": regist,
     }
@@ -1019,6 +1061,7 @@ def main():
     ap.add_argument("--no-c3", action="store_true", help="skip the 128^3 block")
     ap.add_argument("--no-stencil", action="store_true", help="skip the stencil block")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-serving block")
+    ap.add_argument("--no-gamma0", action="store_true", help="skip the gamma = 0 block")
     ap.add_argument("--no-registration", action="store_true",
                     help="skip the 96^3 registration block")
     ap.add_argument("--registration-only", action="store_true",

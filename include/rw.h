@@ -176,13 +176,24 @@ void rw_basis_free(rw_basis* b);
  * hard labels = argmax (ties -> lowest label).  m <= 224; the m x m system lives in one CTA's
  * shared memory, so large m with many labels returns RW_ERR_UNSUPPORTED (e.g. m = 224 with 16
  * labels; m = 200 with 16 labels and m = 224 with 4 labels are supported).
+ *
+ * gamma = 0 (no priors; Sec. II-B, the paragraph after Eq. Fs): L-hat has the null vector
+ * g = D^{1/2} 1 / ||D^{1/2} 1|| (1 / sqrt(N) unnormalized) and E is its pseudo-inverse, so
+ * E F = U - g c with the column sums c = g^T U as further unknowns.  Basis column 0 (the
+ * smallest value) is taken as the null direction and replaced by the exact g; columns 1.. are
+ * used projected orthogonal to g (w_j = g^T q_j from one extra pass over the basis).  The
+ * seeded system gains the border row (1 - g_n^T g_n) c - g_n^T R^T F_s = g_s^T U_s and the
+ * border column -B g_n, solved in the same m x m form with row 0 holding the column-sum
+ * equation; U_n = Q_n' C' + g_n c.  The choice of m (Eq. alpha_1) is made on the basis
+ * [g, Q'].  No priors are read (prior_mode and priors_dev are ignored), rw_solve_info.mu and
+ * sigma are 0.  The graph must be connected (one zero eigenvalue).
  * ---------------------------------------------------------------------------------------- */
 enum { RW_REFINE_JACOBI = 0, RW_REFINE_PCG = 1 };
 enum { RW_BASIS_F16 = 0, RW_BASIS_BF16 = 1, RW_BASIS_F32 = 2 };
 #define RW_MAX_LABELS 16
 
 typedef struct rw_solve_opts {
-  double gamma;          /* prior weight of Eq. (rw_energy); > 0 (gamma = 0 unsupported)     */
+  double gamma;          /* prior weight of Eq. (rw_energy); >= 0 (0: the null-vector form)  */
   int32_t m;             /* eigenvectors used; 0 = adaptive (Sec. III-A-1), else <= basis m  */
   int32_t m_step;        /* adaptive candidates m_step, 2 m_step, ..., m_max (<= 0: 10)      */
   double eps;            /* adaptive accuracy, f_max = S eps^2 (<= 0: 0.1, the paper's)     */
@@ -264,7 +275,8 @@ rw_status rw_last_device_status(const rw_graph* g, void* stream);
  * residual is <= tol (at most iters).  Same seed/prior/output conventions as rw_solve, except
  * that S = 0 is allowed with prior_mode = 1 (registration without landmarks: the seed pointers
  * may then be NULL); each label column is its own system, so more than RW_MAX_LABELS labels
- * are solved in groups of columns.
+ * are solved in groups of columns.  gamma >= 0; gamma = 0 (L_n U_n = -B^T U_s, no priors read)
+ * needs S >= 1.
  * *iters_done (host, may be NULL) receives the iterations run; synchronizes if non-NULL. */
 rw_status rw_solve_pcg(const rw_graph* g, const int32_t* seed_idx_dev,
                        const int32_t* seed_lab_dev, int32_t S, int32_t n_labels,

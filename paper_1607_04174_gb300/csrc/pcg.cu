@@ -444,15 +444,19 @@ extern "C" rw_status rw_solve_pcg(const rw_graph* g, const int32_t* seed_idx_dev
   if (S < 0 || S > 65536 || n_labels < 1 || n_labels > RW_MAX_LABELS) return RW_ERR_INVALID_ARG;
   if (S > 0 && (!seed_idx_dev || !seed_lab_dev)) return RW_ERR_INVALID_ARG;
   if (S == 0 && prior_mode != 1) return RW_ERR_INVALID_ARG;   // no seeds: priors are given
-  if (!(gamma > 0.0)) return gamma == 0.0 ? RW_ERR_UNSUPPORTED : RW_ERR_INVALID_ARG;
-  if (iters < 0 || (prior_mode == 1 && !priors_dev) || (prior_mode == 0 && !g->J))
+  if (!(gamma >= 0.0) || (gamma == 0.0 && S == 0)) return RW_ERR_INVALID_ARG;  // singular
+  if (iters < 0) return RW_ERR_INVALID_ARG;
+  if (gamma > 0.0 && ((prior_mode == 1 && !priors_dev) || (prior_mode == 0 && !g->J)))
     return RW_ERR_INVALID_ARG;
   cudaStream_t st = rw_stream(stream);
   const int lp = n_labels <= 4 ? 4 : (n_labels <= 8 ? 8 : 16);
   float* phat;
   int* seedlab;
+  // gamma = 0: no priors (the P-hat term is gamma P-hat = 0; P-hat is zeroed so it is finite)
   RW_TRY(rw_solve_priors_internal(g, seed_idx_dev, seed_lab_dev, S, n_labels, prior_mode,
-                                  priors_dev, lp, st, &phat, &seedlab, nullptr));
+                                  priors_dev, lp, st, &phat, &seedlab, nullptr, gamma == 0.0));
+  if (gamma == 0.0)
+    RW_CHECK_CUDA(cudaMemsetAsync(phat, 0, sizeof(float) * g->N * lp, st));
   rw_graph* gm = const_cast<rw_graph*>(g);
   if (gm->upd.cap < 8192) return RW_ERR_OOM;
   int* it_dev = reinterpret_cast<int*>(gm->upd.as<char>() + 4096);

@@ -40,7 +40,7 @@ constexpr int kMaxSeeds = 65536;   // seeds per solve (the validation's limit)
 int lpad_of(int L) { return L <= 4 ? 4 : (L <= 8 ? 8 : 16); }
 
 struct Layout {
-  size_t mdev, Bcat, Gcat, Z, C, fu, lu, luinv, part, total;
+  size_t mdev, Bcat, Gcat, Z, C, fu, lu, luinv, part, gnull, partw, wv, nul, lam0, total;
 };
 
 // wcat = 2 mp + 2 lp: the seed-side block [X | Q_s | r0 | U-hat_s] (S x wcat, one row per
@@ -60,6 +60,13 @@ Layout make_layout(int S, int mp, int mq, int lp, int L, int ncand, int nblk_par
   o.lu = take(sizeof(float) * (size_t)mp * mp);   // LU factors of the m x m system, pitch mp
   o.luinv = take(sizeof(float) * (size_t)mp);     // 1 / U_ii
   o.part = take(sizeof(float) * (size_t)nblk_part * mq * lp);
+  // gamma = 0: per seed (g_t, (B-hat g_n)_t), partial sums of Q_s^T g_s, w, the null
+  // coefficients, the values with lambda_0 replaced
+  o.gnull = take(sizeof(float) * 2 * (size_t)S);
+  o.partw = take(sizeof(float) * 16 * (size_t)mq);
+  o.wv = take(sizeof(float) * (size_t)mq);
+  o.nul = take(sizeof(float) * RW_MAX_LABELS);
+  o.lam0 = take(sizeof(double) * (size_t)mq);
   o.total = off;
   return o;
 }
@@ -319,7 +326,8 @@ __global__ void k_seed_gather(const int32_t* __restrict__ idx, const int32_t* __
                               const float* __restrict__ sq, int normalized, int kind, int ndim,
                               int DX, int DY, int DZ, const int32_t* __restrict__ rowptr,
                               const int32_t* __restrict__ colv, const float* __restrict__ ccsr,
-                              float gamma, float* __restrict__ Bcat, int ldb) {
+                              float gamma, float* __restrict__ Bcat, int ldb,
+                              float* __restrict__ gnull, float ginv) {
   rw_grid_wait();
   rw_grid_trigger();
   const int lane = threadIdx.x & 31;
@@ -333,8 +341,11 @@ __global__ void k_seed_gather(const int32_t* __restrict__ idx, const int32_t* __
   if (i < 0 || (int64_t)i >= N || k0 < 0 || k0 >= L) {  // reported by k_seed_scatter
     for (int c = lane; c < mp; c += 32) { qs[c] = 0.f; xs[c] = 0.f; }
     if (lane < lp) { Us[lane] = 0.f; R0[lane] = 0.f; }
+    if (gnull && lane < 2) gnull[2 * t + lane] = 0.f;
     return;
   }
+  // gamma = 0: (B-hat g_n)_t = -sum over unseeded neighbours j of c_ij g_j, g = sq / ||sq||
+  float bnull = 0.f;
   // X row = -sum over unseeded neighbours j of c_ij q_j, kept in registers (mp <= 224)
   const float* qi = Q + (int64_t)i * ldq;
   float acc[7], own[7];
@@ -355,6 +366,7 @@ __global__ void k_seed_gather(const int32_t* __restrict__ idx, const int32_t* __
         const int cc = lane + 32 * q;
         if (cc < mp) acc[q] = fmaf(-c, qj[cc], acc[q]);
       }
+      if (gnull) bnull -= c * sq[j];
     } else if (lane == lj) {
       r0 -= c * sq[j];
     }
@@ -396,6 +408,7 @@ __global__ void k_seed_gather(const int32_t* __restrict__ idx, const int32_t* __
       if (nl[u] < 0) {
 #pragma unroll
         for (int q = 0; q < 7; ++q) acc[q] = fmaf(-nc[u], qn[u][q], acc[q]);
+        bnull -= nc[u] * sn[u];
       } else if (lane == nl[u]) {
         r0 -= nc[u] * sn[u];
       }
@@ -414,6 +427,10 @@ __global__ void k_seed_gather(const int32_t* __restrict__ idx, const int32_t* __
     float u = (lane == k0) ? sq[i] : 0.f;
     Us[lane] = u;
     R0[lane] = (lane < L) ? r0 + gamma * u : 0.f;
+  }
+  if (gnull && lane == 0) {
+    gnull[2 * t] = sq[i] * ginv;
+    gnull[2 * t + 1] = bnull * ginv;
   }
 }
 
@@ -2100,7 +2117,8 @@ __global__ void __launch_bounds__(256)
 k_backproject(const T* __restrict__ Q, int ldq, int cpr, const float* __restrict__ Cg,
               float cscale, const int* __restrict__ seedlab, const float* __restrict__ sq,
               const float* __restrict__ s, int64_t N, int L, const int* __restrict__ mdev,
-              float* __restrict__ xhat, float* __restrict__ U, uint8_t* __restrict__ labels, int* clear_seedlab) {
+              float* __restrict__ xhat, float* __restrict__ U, uint8_t* __restrict__ labels, int* clear_seedlab,
+              const float* __restrict__ nul) {
   rw_grid_wait();
   rw_grid_trigger();
   constexpr int V = Vec16<T>::V;
@@ -2156,7 +2174,7 @@ k_backproject(const T* __restrict__ Q, int ldq, int cpr, const float* __restrict
         val[t] = keep + __shfl_xor_sync(0xffffffff, send, off);
       }
     }
-    const float sum = val[0] + __shfl_xor_sync(0xffffffff, val[0], 1);
+    float sum = val[0] + __shfl_xor_sync(0xffffffff, val[0], 1);
     // even lane 2j holds entry j = r * LP + k
     const int j = lane >> 1;
     const int r = j / LP, k = j % LP;
@@ -2164,6 +2182,7 @@ k_backproject(const T* __restrict__ Q, int ldq, int cpr, const float* __restrict
     const bool writer = (lane & 1) == 0 && i < N;
     int sl = -1;
     if (writer) sl = seedlab[i];
+    if (nul && writer && sl < 0) sum = fmaf(sq[i], __ldg(nul + k), sum);  // gamma = 0: + g_i c_eff
     if (xhat) {
       if (writer) xhat[i * LP + k] = (k >= L) ? 0.f : ((sl >= 0) ? (k == sl ? sq[i] : 0.f) : sum);
     } else {
@@ -2409,7 +2428,8 @@ __device__ __forceinline__ void backproject_rows(const T* __restrict__ Qp, int64
                                                  const float* __restrict__ sq,
                                                  const float* __restrict__ s, int L,
                                                  float* __restrict__ xhat, float* __restrict__ U,
-                                                 uint8_t* __restrict__ labels, int* clear_seedlab) {
+                                                 uint8_t* __restrict__ labels, int* clear_seedlab,
+                                                 const float* nul) {
   constexpr int CPI = kBackChunks / VPI;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < N; i0 += VPI * stride) {
@@ -2456,6 +2476,17 @@ __device__ __forceinline__ void backproject_rows(const T* __restrict__ Qp, int64
         }
       }
     }
+    if (nul) {  // gamma = 0: + g_i c_eff on the unseeded rows (g_i = sq_i / ||sq||, in nul)
+#pragma unroll
+      for (int w = 0; w < VPI; ++w) {
+        const int64_t i = i0 + w * stride;
+        if (i < N && sl[w] < 0) {
+          const float sqi = sq[i];
+#pragma unroll
+          for (int k = 0; k < LP; ++k) acc[w][k] = fmaf(sqi, nul[k], acc[w][k]);
+        }
+      }
+    }
 #pragma unroll
     for (int w = 0; w < VPI; ++w) {
       const int64_t i = i0 + w * stride;
@@ -2497,27 +2528,30 @@ k_backproject_panel(const T* __restrict__ Qp, int64_t N, int nchunk_max,
                     const float* __restrict__ Cg, float cscale, const int* __restrict__ seedlab,
                     const float* __restrict__ sq, const float* __restrict__ s, int L,
                     const int* __restrict__ mdev, float* __restrict__ xhat,
-                    float* __restrict__ U, uint8_t* __restrict__ labels, int* clear_seedlab) {
+                    float* __restrict__ U, uint8_t* __restrict__ labels, int* clear_seedlab,
+                    const float* __restrict__ nulg) {
   rw_grid_wait();
   rw_grid_trigger();
-  extern __shared__ float Cs[];  // (8 nchunk_max, rounded up to kBackChunks chunks) x LP
+  extern __shared__ float Cs[];  // (8 nchunk_max, rounded up to kBackChunks chunks) x LP, + LP
   const int m = mdev[0];
   const int nch = min((m + 7) / 8, nchunk_max);
   const int ncs = (nchunk_max + kBackChunks - 1) / kBackChunks * kBackChunks;
   for (int e = threadIdx.x; e < ncs * 8 * LP; e += blockDim.x)
     Cs[e] = e < nchunk_max * 8 * LP ? Cg[e] * cscale : 0.f;
+  float* nul = nulg ? Cs + ncs * 8 * LP : nullptr;
+  if (nulg && threadIdx.x < LP) nul[threadIdx.x] = nulg[threadIdx.x];
   __syncthreads();
   // seed rows discard the products (their flag is loaded with the first chunks)
   if constexpr (LP <= 8) {  // (16 labels: the four-voxel form would spill)
     if (nch <= kBackChunks / 4) {
-      backproject_rows<T, LP, 4>(Qp, N, nch, Cs, seedlab, sq, s, L, xhat, U, labels, clear_seedlab);
+      backproject_rows<T, LP, 4>(Qp, N, nch, Cs, seedlab, sq, s, L, xhat, U, labels, clear_seedlab, nul);
       return;
     }
   }
   if (nch <= kBackChunks / 2)
-    backproject_rows<T, LP, 2>(Qp, N, nch, Cs, seedlab, sq, s, L, xhat, U, labels, clear_seedlab);
+    backproject_rows<T, LP, 2>(Qp, N, nch, Cs, seedlab, sq, s, L, xhat, U, labels, clear_seedlab, nul);
   else
-    backproject_rows<T, LP, 1>(Qp, N, nch, Cs, seedlab, sq, s, L, xhat, U, labels, clear_seedlab);
+    backproject_rows<T, LP, 1>(Qp, N, nch, Cs, seedlab, sq, s, L, xhat, U, labels, clear_seedlab, nul);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -2714,7 +2748,7 @@ template <typename T, int LP>
 rw_status launch_proj_back(bool back, const T* Q, int ldq, const float* phat,
                            const int* seedlab, const rw_graph* g, const int* mdev, float* part,
                            int nblk, const float* C, float cscale, float* xhat, float* U,
-                           uint8_t* labels, int L, int* clear, cudaStream_t st) {
+                           uint8_t* labels, int L, int* clear, const float* nul, cudaStream_t st) {
   constexpr int V = Vec16<T>::V;
   const int cpr = ldq / V;
   if constexpr (V == 8) {  // 16-bit copies: panel-major layout, ldq = 8 x chunks
@@ -2734,9 +2768,9 @@ rw_status launch_proj_back(bool back, const T* Q, int ldq, const float* phat,
                   rpb, part);
       }
     } else {
-      const size_t shm = sizeof(float) * (size_t)((nchunk + kBackChunks - 1) / kBackChunks * kBackChunks) * 8 * LP;
+      const size_t shm = sizeof(float) * ((size_t)((nchunk + kBackChunks - 1) / kBackChunks * kBackChunks) * 8 * LP + LP);
       RW_LAUNCH((k_backproject_panel<T, LP>), nblk, 256, shm, st, Q, g->N, nchunk, C, cscale, seedlab,
-                                                        g->sq, g->s, L, mdev, xhat, U, labels, clear);
+                                                        g->sq, g->s, L, mdev, xhat, U, labels, clear, nul);
     }
     RW_LAUNCH_CHECK();
     return RW_OK;
@@ -2752,10 +2786,10 @@ rw_status launch_proj_back(bool back, const T* Q, int ldq, const float* phat,
   } else {
     if (cpr <= 32)
       RW_LAUNCH((k_backproject<T, LP, 1>), nblk, 256, 0, st, Q, ldq, cpr, C, cscale, seedlab, g->sq, g->s,
-                                                   g->N, L, mdev, xhat, U, labels, clear);
+                                                   g->N, L, mdev, xhat, U, labels, clear, nul);
     else if (cpr <= 64)
       RW_LAUNCH((k_backproject<T, LP, 2>), nblk, 256, 0, st, Q, ldq, cpr, C, cscale, seedlab, g->sq, g->s,
-                                                   g->N, L, mdev, xhat, U, labels, clear);
+                                                   g->N, L, mdev, xhat, U, labels, clear, nul);
     else
       return RW_ERR_UNSUPPORTED;
   }
@@ -2767,12 +2801,151 @@ rw_status launch_proj_back(bool back, const T* Q, int ldq, const float* phat,
 template <typename T>
 rw_status proj_back(int lp, bool back, const T* Q, int ldq, const float* phat, const int* seedlab,
                     const rw_graph* g, const int* mdev, float* part, int nblk, const float* C,
-                    float cscale, float* xhat, float* U, uint8_t* labels, int L, cudaStream_t st, int* clear = nullptr) {
+                    float cscale, float* xhat, float* U, uint8_t* labels, int L, cudaStream_t st, int* clear = nullptr,
+                    const float* nul = nullptr) {
   switch (lp) {
-    case 4: return launch_proj_back<T, 4>(back, Q, ldq, phat, seedlab, g, mdev, part, nblk, C, cscale, xhat, U, labels, L, clear, st);
-    case 8: return launch_proj_back<T, 8>(back, Q, ldq, phat, seedlab, g, mdev, part, nblk, C, cscale, xhat, U, labels, L, clear, st);
-    default: return launch_proj_back<T, 16>(back, Q, ldq, phat, seedlab, g, mdev, part, nblk, C, cscale, xhat, U, labels, L, clear, st);
+    case 4: return launch_proj_back<T, 4>(back, Q, ldq, phat, seedlab, g, mdev, part, nblk, C, cscale, xhat, U, labels, L, clear, nul, st);
+    case 8: return launch_proj_back<T, 8>(back, Q, ldq, phat, seedlab, g, mdev, part, nblk, C, cscale, xhat, U, labels, L, clear, nul, st);
+    default: return launch_proj_back<T, 16>(back, Q, ldq, phat, seedlab, g, mdev, part, nblk, C, cscale, xhat, U, labels, L, clear, nul, st);
   }
+}
+
+// ---------------------------------------------------------------------------------------
+// gamma = 0 (Sec. II-B, after Eq. Fs): L-hat has the null vector g = sq / ||sq|| and E is its
+// pseudo-inverse, so the seeded system gains the column sums c = g^T U-hat as unknowns.  The
+// stored column 0 is taken as the null direction and replaced by g, the other columns are
+// projected orthogonal to g (Q' = Q - g w^T, w_j = g^T q_j), and row 0 of the m x m system
+// becomes the column-sum equation:
+//   k_seed_gather  also writes g_t and (B-hat g_n)_t per seed
+//   k_null_fill    P-hat column 0 := g (the projection then gives w^n = Q_n^T g_n)
+//   k_null_w       partial sums of p = Q_s^T g_s (fixed order)
+//   k_null_rows    w = w^n + p; seed rows Q_s' = [g_s, Q_s - g_s w^T], X' = [B g_n, X - B g_n w^T]
+//   (seed Gram: K, G, h, b on the basis [g, Q'])
+//   k_null_row0    s = g_s^T g_s; M_00 = s, M_0j = -(w^n_j - w_j (1 - s)), h_0 = g_s^T U-hat_s
+//   (adaptive m, LU, C = M^{-1} h)
+//   k_null_coef    c_eff = c - w^T C' (C row 0 := 0), added as g_i c_eff by the back-projection
+// ---------------------------------------------------------------------------------------
+template <int LP>
+__global__ void k_null_fill(float* __restrict__ phat, const float* __restrict__ sq, int64_t N,
+                            float ginv) {
+  rw_grid_wait();
+  rw_grid_trigger();
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    float4* row = reinterpret_cast<float4*>(phat + i * LP);
+    row[0] = make_float4(sq[i] * ginv, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int k4 = 1; k4 < LP / 4; ++k4) row[k4] = make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+}
+
+constexpr int kNullSplit = 16;   // seed ranges of the p = Q_s^T g_s partial sums (the layout's partw)
+
+// grid (ceil(mmax / 32), ny): block (x, y) sums g_t Q_s[t, c] over seed range y for the 32
+// columns c of x; warps take seeds strided by 8 and are added in order
+__global__ void __launch_bounds__(256)
+k_null_w(const float* __restrict__ Qs, int ldb, const float* __restrict__ gnull, int S, int mmax,
+         float* __restrict__ partw, int mq) {
+  rw_grid_wait();
+  rw_grid_trigger();
+  __shared__ float red[8][32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int c = blockIdx.x * 32 + lane;
+  const int chunk = (S + gridDim.y - 1) / gridDim.y;
+  const int t0 = blockIdx.y * chunk, t1 = min(S, t0 + chunk);
+  float acc = 0.f;
+  if (c < mmax)
+    for (int t = t0 + warp; t < t1; t += 8) acc = fmaf(gnull[2 * t], Qs[(int64_t)t * ldb + c], acc);
+  red[warp][lane] = acc;
+  __syncthreads();
+  if (warp == 0 && c < mmax) {
+    float v = 0.f;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) v += red[w][lane];
+    partw[(size_t)blockIdx.y * mq + c] = v;
+  }
+}
+
+__global__ void __launch_bounds__(256)
+k_null_rows(float* __restrict__ Bcat, int ldb, int mp, const float* __restrict__ gnull, int S,
+            int mmax, const float* __restrict__ partw, int ny, int mq,
+            const float* __restrict__ Z, int lp, float* __restrict__ wv) {
+  rw_grid_wait();
+  rw_grid_trigger();
+  __shared__ float w[kMaxSmallM];
+  for (int j = threadIdx.x; j < mmax; j += blockDim.x) {
+    float v = Z[(size_t)j * lp];                       // w^n_j
+    for (int y = 0; y < ny; ++y) v += partw[(size_t)y * mq + j];
+    w[j] = j == 0 ? 0.f : v;
+    if (blockIdx.x == 0) wv[j] = w[j];
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  for (int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < S;
+       t += (gridDim.x * blockDim.x) >> 5) {
+    const float gt = gnull[2 * t], bt = gnull[2 * t + 1];
+    float* xs = Bcat + (int64_t)t * ldb;
+    float* qs = xs + mp;
+    for (int c = lane; c < mmax; c += 32) {
+      if (c == 0) {
+        xs[0] = bt;
+        qs[0] = gt;
+      } else {
+        xs[c] = fmaf(-bt, w[c], xs[c]);
+        qs[c] = fmaf(-gt, w[c], qs[c]);
+      }
+    }
+  }
+}
+
+// one CTA: row 0 of K, h (M = diag(lambda0) - K, lambda0_0 = s) after the seed Gram; Z zeroed
+// once w^n is read (gamma Z = 0 then needs no 0 x inf guard)
+__global__ void __launch_bounds__(256)
+k_null_row0(float* __restrict__ Gcat, int mp, int lp, int mmax, const float* __restrict__ wv,
+            float* __restrict__ Z, int mq, const double* __restrict__ lam,
+            double* __restrict__ lam0, float* __restrict__ lgam) {
+  rw_grid_wait();
+  rw_grid_trigger();
+  const float sv = Gcat[mp];          // G_00 = g_s^T g_s
+  for (int j = threadIdx.x; j < mmax; j += blockDim.x) {
+    Gcat[j] = j == 0 ? 0.f : Z[(size_t)j * lp] - wv[j] * (1.f - sv);
+    lam0[j] = j == 0 ? (double)sv : lam[j];
+  }
+  if (threadIdx.x < lp) Gcat[2 * mp + threadIdx.x] = Gcat[2 * mp + lp + threadIdx.x];
+  if (threadIdx.x == 0) lgam[0] = sv;
+  __syncthreads();
+  for (int e = threadIdx.x; e < mq * lp; e += blockDim.x) Z[e] = 0.f;
+}
+
+// one CTA, a warp per label: c_eff_k = C_0k - sum_{j >= 1} w_j C_jk (lanes strided, butterfly),
+// nul_k = c_eff_k / ||sq||, C_0k := 0
+__global__ void __launch_bounds__(256)
+k_null_coef(float* __restrict__ C, int lp, int L, const int* __restrict__ mdev,
+            const float* __restrict__ wv, float ginv, float* __restrict__ nul) {
+  rw_grid_wait();
+  rw_grid_trigger();
+  __shared__ float ce[RW_MAX_LABELS];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int m = mdev[0];
+  for (int k = warp; k < lp; k += nw) {
+    float v = 0.f;
+    for (int j = 1 + lane; j < m; j += 32) v = fmaf(wv[j], C[(size_t)j * lp + k], v);
+    v = warp_sum(v);
+    if (lane == 0) ce[k] = k < L ? (C[k] - v) * ginv : 0.f;
+  }
+  __syncthreads();
+  if (threadIdx.x < lp) {
+    nul[threadIdx.x] = ce[threadIdx.x];
+    C[threadIdx.x] = 0.f;
+  }
+}
+
+// An empty launch between k_adapt_lu and k_small_rhs when no projection runs between them
+// (gamma = 0): k_small_rhs copies the factors in ahead of its own grid dependency wait, which
+// is safe only two launches behind their producer.
+__global__ void k_pdl_fence(int) {
+  rw_grid_wait();
+  rw_grid_trigger();
 }
 
 // BF16 copy in the panel-major layout of the 16-bit basis copies
@@ -2963,12 +3136,14 @@ static rw_status validate_solve(const rw_graph* g, const rw_basis* b, const int3
   if (!g || !b || !si || !sl || !o || !prob) return RW_ERR_INVALID_ARG;
   if (b->N != g->N) return RW_ERR_INVALID_ARG;
   if (S < 1 || S > 65536 || L < 1 || L > RW_MAX_LABELS) return RW_ERR_INVALID_ARG;
-  if (!(o->gamma > 0.0)) return o->gamma == 0.0 ? RW_ERR_UNSUPPORTED : RW_ERR_INVALID_ARG;
+  if (!(o->gamma >= 0.0)) return RW_ERR_INVALID_ARG;   // negative or NaN
   if (o->m < 0 || o->m > b->m) return RW_ERR_INVALID_ARG;
   if (o->refine_steps < 0 || o->refine_steps > 100000) return RW_ERR_INVALID_ARG;
-  if (o->prior_mode == 1 && !priors) return RW_ERR_INVALID_ARG;
   if (o->prior_mode != 0 && o->prior_mode != 1) return RW_ERR_INVALID_ARG;
-  if (o->prior_mode == 0 && !g->J) return RW_ERR_INVALID_ARG;
+  if (o->gamma > 0.0) {   // gamma = 0 takes no priors
+    if (o->prior_mode == 1 && !priors) return RW_ERR_INVALID_ARG;
+    if (o->prior_mode == 0 && !g->J) return RW_ERR_INVALID_ARG;
+  }
   if (o->basis_format < RW_BASIS_F16 || o->basis_format > RW_BASIS_F32) return RW_ERR_INVALID_ARG;
   if (o->refine_mode != RW_REFINE_JACOBI && o->refine_mode != RW_REFINE_PCG) return RW_ERR_INVALID_ARG;
   int mmax = o->m > 0 ? o->m : b->m;
@@ -3002,6 +3177,7 @@ extern "C" rw_status rw_solve(const rw_graph* g, const rw_basis* b, const int32_
   const int L = n_labels, lp = lpad_of(L);
   const int mp = b->ld32;
   const double gamma = opts->gamma;
+  const bool g0 = gamma == 0.0;   // no priors: the null-vector form of Sec. II-B
   const int m_step = opts->m_step > 0 ? opts->m_step : 10;
   const double eps = opts->eps > 0 ? opts->eps : 0.1;
   const float omega = (float)(opts->omega > 0 ? std::min(opts->omega, 1.0) : 0.8);
@@ -3046,17 +3222,74 @@ extern "C" rw_status rw_solve(const rw_graph* g, const rw_basis* b, const int32_
   float* G = Gcat + mp;                // Q_s^T Q_s
   float* h = Gcat + 2 * mp;            // Q_s^T r0
   float* bv = Gcat + 2 * mp + lp;      // Q_s^T U-hat_s
+  // rho = sqrt(1^T D 1) with the normalized Laplacian (Sec. III-A-1), else sqrt(N); the unit
+  // null vector of L-hat is sq / rho
+  const double rho = g->normalized ? sqrt(g->dsum) : sqrt((double)g->N);
+  const float ginv = (float)(1.0 / rho);
+  float* gnull = g0 ? reinterpret_cast<float*>(P(lay.gnull)) : nullptr;
+  float* wv = reinterpret_cast<float*>(P(lay.wv));
+  float* nul = reinterpret_cast<float*>(P(lay.nul));
+  double* lam0 = reinterpret_cast<double*>(P(lay.lam0));
   RW_LAUNCH(k_seed_gather, rw_blocks((int64_t)S * 32, 256), 256, 0, st, 
       seed_idx_dev, seed_lab_dev, S, L, lp, g->N, b->Q32, b->ld32, mp, seedlab, g->cw, g->d,
       g->sq, g->normalized, g->kind, g->ndim, g->dims[0], g->dims[1], g->dims[2], g->rowptr,
-      g->col, g->ccsr, (float)gamma, Bcat, wcat);
+      g->col, g->ccsr, (float)gamma, Bcat, wcat, gnull, ginv);
+  float* part = reinterpret_cast<float*>(P(lay.part));
+  float* Z = reinterpret_cast<float*>(P(lay.Z));
+  float* lgam = Z + (size_t)mq * lp;
+  int fmt = opts->basis_format;
+  if (fmt == RW_BASIS_BF16 && !b->Qbf) {
+    rw_basis* bm = const_cast<rw_basis*>(b);
+    RW_CHECK_CUDA(cudaMalloc(&bm->Qbf, sizeof(__nv_bfloat16) * b->N * b->ld16));
+    k_f32_to_bf16<<<rw_blocks(b->N * b->ld16, 256), 256, 0, st>>>(b->Q32, b->N, b->m, b->ld32,
+                                                                   bm->Qbf, b->ld16);
+    RW_LAUNCH_CHECK();
+  }
+  int ldq_e = fmt == RW_BASIS_F32 ? b->ld32 : b->ld16;
+  // projection blocks: the chunk-major 16-bit kernel takes the tuned count per SM (2 by
+  // default: more rows per block, fewer partials to add); the FP32 row kernel 4 per SM
+  int proj_per_sm = 2, back_per_sm = 3;
+  launch_shape(g->N, &proj_per_sm, &back_per_sm);
+  const int nblk_p = fmt == RW_BASIS_F32 ? nblk : proj_per_sm * sms;
+  float zscale = fmt == RW_BASIS_F16 ? 1.f / b->qscale : 1.f;
+  float cscale = fmt == RW_BASIS_F16 ? 1.f / b->qscale : 1.f;
+  auto project = [&]() -> rw_status {
+    if (fmt == RW_BASIS_F16)
+      RW_TRY(proj_back<__half>(lp, false, b->Q16, ldq_e, phat, seedlab, g, mdev, part, nblk_p, nullptr, 0.f, nullptr, nullptr, nullptr, L, st));
+    else if (fmt == RW_BASIS_BF16)
+      RW_TRY(proj_back<__nv_bfloat16>(lp, false, b->Qbf, ldq_e, phat, seedlab, g, mdev, part, nblk_p, nullptr, 0.f, nullptr, nullptr, nullptr, L, st));
+    else
+      RW_TRY(proj_back<float>(lp, false, b->Q32, ldq_e, phat, seedlab, g, mdev, part, nblk_p, nullptr, 0.f, nullptr, nullptr, nullptr, L, st));
+    RW_LAUNCH(k_reduce_partials, rw_blocks((int64_t)std::max(mq * lp, m_max) * 32, 256), 256, 0, st, 
+        part, nblk_p, ldq_e, lp, mq, zscale, Z, b->lam, gamma, m_max, lgam);
+    return RW_OK;
+  };
+  if (g0) {
+    // w^n = Q_n^T g_n over all m_max columns (P-hat column 0 := g), then the seed rows of the
+    // basis [g, Q']
+    const int fblk = (int)std::min<int64_t>(rw_blocks(g->N, 256), 8 * sms);
+    if (lp == 4) RW_LAUNCH(k_null_fill<4>, fblk, 256, 0, st, phat, g->sq, g->N, ginv);
+    else if (lp == 8) RW_LAUNCH(k_null_fill<8>, fblk, 256, 0, st, phat, g->sq, g->N, ginv);
+    else RW_LAUNCH(k_null_fill<16>, fblk, 256, 0, st, phat, g->sq, g->N, ginv);
+    RW_LAUNCH(k_set_m, 1, 32, 0, st, mdev, m_max);
+    RW_TRY(project());
+    float* partw = reinterpret_cast<float*>(P(lay.partw));
+    const int ny = std::max(1, std::min(kNullSplit, (S + 255) / 256));
+    RW_LAUNCH(k_null_w, dim3((m_max + 31) / 32, ny), 256, 0, st, Qs, wcat, gnull, S, m_max,
+              partw, mq);
+    const int rblk = (int)std::min<int64_t>((S + 7) / 8, 2 * sms);
+    RW_LAUNCH(k_null_rows, rblk, 256, 0, st, Bcat, wcat, mp, gnull, S, m_max, partw, ny, mq, Z,
+              lp, wv);
+  }
   RW_TRY(seed_gram(Qs, wcat, Bcat, wcat, S, m_max, wcat, Gcat, wcat, st));
-  RW_TRY(launch_priors(g, L, opts->prior_mode, priors_dev, lp, phases ? 0 : 1, st));
+  if (g0)
+    RW_LAUNCH(k_null_row0, 1, 256, 0, st, Gcat, mp, lp, m_max, wv, Z, mq, b->lam, lam0, lgam);
+  else
+    RW_TRY(launch_priors(g, L, opts->prior_mode, priors_dev, lp, phases ? 0 : 1, st));
+  const double* lamv = g0 ? lam0 : b->lam;
   double* fu = reinterpret_cast<double*>(P(lay.fu));
   double* fsel = fu + (size_t)(ncand + 1) * RW_MAX_LABELS;
   RW_TRY(mark(2));
-  // rho = sqrt(1^T D 1) with the normalized Laplacian (Sec. III-A-1), else sqrt(N)
-  const double rho = g->normalized ? sqrt(g->dsum) : sqrt((double)g->N);
   const double fmax = (double)S * eps * eps;
   float* Fac = reinterpret_cast<float*>(P(lay.lu));
   float* luinv = reinterpret_cast<float*>(P(lay.luinv));
@@ -3068,13 +3301,13 @@ extern "C" rw_status rw_solve(const rw_graph* g, const rw_basis* b, const int32_
   if (fused) {
     if (lp == 4)
       RW_TRY(launch_adapt_lu<4>(shm_fused, st, G, bv, Qs, Us, wcat, S, L, m_max, m_step, rho, fmax,
-                                adaptive, K, b->lam, gamma, Fac, mp, luinv, mdev, fsel));
+                                adaptive, K, lamv, gamma, Fac, mp, luinv, mdev, fsel));
     else if (lp == 8)
       RW_TRY(launch_adapt_lu<8>(shm_fused, st, G, bv, Qs, Us, wcat, S, L, m_max, m_step, rho, fmax,
-                                adaptive, K, b->lam, gamma, Fac, mp, luinv, mdev, fsel));
+                                adaptive, K, lamv, gamma, Fac, mp, luinv, mdev, fsel));
     else
       RW_TRY(launch_adapt_lu<16>(shm_fused, st, G, bv, Qs, Us, wcat, S, L, m_max, m_step, rho,
-                                 fmax, adaptive, K, b->lam, gamma, Fac, mp, luinv, mdev, fsel));
+                                 fmax, adaptive, K, lamv, gamma, Fac, mp, luinv, mdev, fsel));
   } else if (adaptive) {
     const size_t shm = sizeof(float) * ((size_t)m_max * (m_max | 1) + 3 * (size_t)L * m_max);
     if (lp == 4) {
@@ -3095,34 +3328,9 @@ extern "C" rw_status rw_solve(const rw_graph* g, const rw_basis* b, const int32_
     RW_LAUNCH(k_set_m, 1, 32, 0, st, mdev, m_max);
   }
   RW_TRY(mark(3));
-  // Z = Q_n^T P-hat_n
-  float* part = reinterpret_cast<float*>(P(lay.part));
-  float* Z = reinterpret_cast<float*>(P(lay.Z));
-  float* lgam = Z + (size_t)mq * lp;
-  int fmt = opts->basis_format;
-  if (fmt == RW_BASIS_BF16 && !b->Qbf) {
-    rw_basis* bm = const_cast<rw_basis*>(b);
-    RW_CHECK_CUDA(cudaMalloc(&bm->Qbf, sizeof(__nv_bfloat16) * b->N * b->ld16));
-    k_f32_to_bf16<<<rw_blocks(b->N * b->ld16, 256), 256, 0, st>>>(b->Q32, b->N, b->m, b->ld32,
-                                                                   bm->Qbf, b->ld16);
-    RW_LAUNCH_CHECK();
-  }
-  int ldq_e = fmt == RW_BASIS_F32 ? b->ld32 : b->ld16;
-  // projection blocks: the chunk-major 16-bit kernel takes the tuned count per SM (2 by
-  // default: more rows per block, fewer partials to add); the FP32 row kernel 4 per SM
-  int proj_per_sm = 2, back_per_sm = 3;
-  launch_shape(g->N, &proj_per_sm, &back_per_sm);
-  const int nblk_p = fmt == RW_BASIS_F32 ? nblk : proj_per_sm * sms;
-  float zscale = fmt == RW_BASIS_F16 ? 1.f / b->qscale : 1.f;
-  float cscale = fmt == RW_BASIS_F16 ? 1.f / b->qscale : 1.f;
-  if (fmt == RW_BASIS_F16)
-    RW_TRY(proj_back<__half>(lp, false, b->Q16, ldq_e, phat, seedlab, g, mdev, part, nblk_p, nullptr, 0.f, nullptr, nullptr, nullptr, L, st));
-  else if (fmt == RW_BASIS_BF16)
-    RW_TRY(proj_back<__nv_bfloat16>(lp, false, b->Qbf, ldq_e, phat, seedlab, g, mdev, part, nblk_p, nullptr, 0.f, nullptr, nullptr, nullptr, L, st));
-  else
-    RW_TRY(proj_back<float>(lp, false, b->Q32, ldq_e, phat, seedlab, g, mdev, part, nblk_p, nullptr, 0.f, nullptr, nullptr, nullptr, L, st));
-  RW_LAUNCH(k_reduce_partials, rw_blocks((int64_t)std::max(mq * lp, m_max) * 32, 256), 256, 0, st, 
-      part, nblk_p, ldq_e, lp, mq, zscale, Z, b->lam, gamma, m_max, lgam);
+  // Z = Q_n^T P-hat_n (gamma = 0: no priors; Z was zeroed by k_null_row0)
+  if (!g0) RW_TRY(project());
+  else if (fused) RW_LAUNCH(k_pdl_fence, 1, 32, 0, st, 0);
   RW_TRY(mark(4));
   // small system
   float* C = reinterpret_cast<float*>(P(lay.C));
@@ -3160,6 +3368,7 @@ extern "C" rw_status rw_solve(const rw_graph* g, const rw_basis* b, const int32_
     }
     RW_LAUNCH_CHECK();
   }
+  if (g0) RW_LAUNCH(k_null_coef, 1, 256, 0, st, C, lp, L, mdev, wv, ginv, nul);
   RW_TRY(mark(5));
   // back-projection (+ refinement); the 16-bit kernel holds three blocks per SM
   const int nblk_b = fmt == RW_BASIS_F32 ? nblk : back_per_sm * sms;
@@ -3172,12 +3381,13 @@ extern "C" rw_status rw_solve(const rw_graph* g, const rw_basis* b, const int32_
     xh0 = ws.xhat[0].as<float>();
     xh1 = ws.xhat[1].as<float>();
   }
+  const float* nulp = g0 ? nul : nullptr;
   if (fmt == RW_BASIS_F16)
-    RW_TRY(proj_back<__half>(lp, true, b->Q16, ldq_e, phat, seedlab, g, mdev, part, nblk_b, C, cscale, xh0, prob_dev, labels_dev, L, st, steps == 0 ? seedlab : nullptr));
+    RW_TRY(proj_back<__half>(lp, true, b->Q16, ldq_e, phat, seedlab, g, mdev, part, nblk_b, C, cscale, xh0, prob_dev, labels_dev, L, st, steps == 0 ? seedlab : nullptr, nulp));
   else if (fmt == RW_BASIS_BF16)
-    RW_TRY(proj_back<__nv_bfloat16>(lp, true, b->Qbf, ldq_e, phat, seedlab, g, mdev, part, nblk_b, C, cscale, xh0, prob_dev, labels_dev, L, st, steps == 0 ? seedlab : nullptr));
+    RW_TRY(proj_back<__nv_bfloat16>(lp, true, b->Qbf, ldq_e, phat, seedlab, g, mdev, part, nblk_b, C, cscale, xh0, prob_dev, labels_dev, L, st, steps == 0 ? seedlab : nullptr, nulp));
   else
-    RW_TRY(proj_back<float>(lp, true, b->Q32, ldq_e, phat, seedlab, g, mdev, part, nblk_b, C, cscale, xh0, prob_dev, labels_dev, L, st, steps == 0 ? seedlab : nullptr));
+    RW_TRY(proj_back<float>(lp, true, b->Q32, ldq_e, phat, seedlab, g, mdev, part, nblk_b, C, cscale, xh0, prob_dev, labels_dev, L, st, steps == 0 ? seedlab : nullptr, nulp));
   RW_TRY(mark(6));
   if (steps > 0) {
     if (opts->refine_mode == RW_REFINE_JACOBI) {
@@ -3217,8 +3427,8 @@ extern "C" rw_status rw_solve(const rw_graph* g, const rw_basis* b, const int32_
     const double* f64 = reinterpret_cast<const double*>(hb + 256);
     for (int k = 0; k < L; ++k) {
       info->f[k] = adaptive ? fh[k] : 0.0;
-      info->mu[k] = f64[k];
-      info->sigma[k] = f64[16 + k];
+      info->mu[k] = g0 ? 0.0 : f64[k];          // no Gaussian fit without priors
+      info->sigma[k] = g0 ? 0.0 : f64[16 + k];
     }
     if (phases)
       for (int k = 0; k < RW_NUM_PHASES; ++k)

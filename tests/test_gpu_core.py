@@ -254,8 +254,8 @@ def test_bad_arguments_raise(c1):
         with pytest.raises(rw.RWError):
             rw.rw_solve(g, b, to_dev(c1["si"]), to_dev(badl), 2, prob, m=20)
         with pytest.raises(rw.RWError) as e:
-            rw.rw_solve(g, b, to_dev(c1["si"]), to_dev(c1["sl"]), 2, prob, m=20, gamma=0.0)
-        assert e.value.status == rw.RW_ERR_UNSUPPORTED
+            rw.rw_solve(g, b, to_dev(c1["si"]), to_dev(c1["sl"]), 2, prob, m=20, gamma=-1.0)
+        assert e.value.status == rw.RW_ERR_INVALID_ARG
         with pytest.raises(rw.RWError):
             rw.rw_solve(g, b, to_dev(c1["si"]), to_dev(c1["sl"]), 2, prob, m=51)
         # the handle still works after the errors
