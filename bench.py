@@ -764,6 +764,7 @@ def gpu_arm(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     build.build()
+    rw.rw_set_tc_passes(args.tc_passes)
     peaks = {}
     pk = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(pk):
@@ -1015,6 +1016,7 @@ def gpu_arm(args):
         "config": {"workload": WORKLOAD, "size": [SIZE, SIZE], "labels": LABELS,
                    "seeds_per_label": SEEDS_PER_LABEL, "m_max": M, "eps": EPS,
                    "refine_steps": REFINE, "basis_format": "f16-scaled",
+                   "tc_passes": args.tc_passes,
                    "l2": "flushed (256 MB write) before every timed step",
                    "parallelism": f"replicas x{world}"},
         "p50_ms": float(np.percentile(step_ms, 50)), "p99_ms": float(np.percentile(step_ms, 99)),
@@ -1062,6 +1064,9 @@ def main():
     ap.add_argument("--no-stencil", action="store_true", help="skip the stencil block")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-serving block")
     ap.add_argument("--no-gamma0", action="store_true", help="skip the gamma = 0 block")
+    ap.add_argument("--tc-passes", type=int, default=0, choices=[0, 1, 2, 3],
+                    help="basis passes on the tensor cores: bit 0 projection, bit 1 "
+                         "back-projection (default 0: both on CUDA cores)")
     ap.add_argument("--no-registration", action="store_true",
                     help="skip the 96^3 registration block")
     ap.add_argument("--registration-only", action="store_true",

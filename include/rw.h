@@ -423,6 +423,13 @@ rw_status rw_rayleigh_quotients_noalloc(const rw_graph* g, const float* Q_dev, i
  * N <= n_max (up to 16 size classes, ascending; n_max <= 0 clears the table); without an entry
  * the projection uses 2 and the back-projection 3.  proj_per_sm in [1, 4], back_per_sm in
  * [1, 8].  The project's autotuner (paper_1607_04174_gb300/autotune.py) measures the table.
+ * rw_set_tc_passes selects, process-wide, the tensor-core kernels or the CUDA-core kernels for
+ * the two passes over a 16-bit basis copy in rw_solve, rw_solve_unseeded and the batch calls:
+ * bit 0 of mask = the projection Z = Q_n^T P_n, bit 1 = the back-projection U_n = Q_n C
+ * (Eq. U_lin_comb); 0 (both on CUDA cores) is the default, 3 puts both on tensor cores; other
+ * values return RW_ERR_INVALID_ARG.  The launch-shape table applies to the CUDA-core kernels
+ * only (the tensor-core ones run one block per SM).  Copies wider than 256 columns and the FP32
+ * basis always use the CUDA-core kernels.  Takes effect for launches after the call.
  * ---------------------------------------------------------------------------------------- */
 typedef struct rw_batch rw_batch;
 typedef struct rw_batch_item {
@@ -444,6 +451,7 @@ rw_status rw_batch_capture(rw_batch* bt, const rw_batch_item* items, int32_t n,
                            const rw_solve_opts* opts, void* stream, int32_t* updated_in_place);
 rw_status rw_batch_launch(rw_batch* bt, void* stream);
 rw_status rw_set_launch_shape(int64_t n_max, int32_t proj_per_sm, int32_t back_per_sm);
+rw_status rw_set_tc_passes(int32_t mask);
 
 /* ------------------------------------------------------------------------------------------
  * Registration (RWIR, Sec. II-A: the K labels are displacement vectors; Sec. III-A-2; Sec. IV-B).

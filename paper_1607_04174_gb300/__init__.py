@@ -378,6 +378,12 @@ def rw_set_launch_shape(n_max, proj_per_sm, back_per_sm):
                   "rw_set_launch_shape")
 
 
+def rw_set_tc_passes(mask):
+    """bit 0: projection on the tensor cores, bit 1: back-projection (0 = both on CUDA cores,
+    the default; 3 = both on tensor cores)."""
+    return _check(abi.lib().rw_set_tc_passes(int(mask)), "rw_set_tc_passes")
+
+
 def load_launch_shapes(path=None):
     """Installs the launch-shape table measured by the project's autotuner
     (paper_1607_04174_gb300/autotune.py); returns the entries installed."""

@@ -122,6 +122,7 @@ PROTOTYPES = {
                                C.POINTER(I32)]),
     "rw_batch_launch": (I32, [P, P]),
     "rw_set_launch_shape": (I32, [I64, I32, I32]),
+    "rw_set_tc_passes": (I32, [I32]),
     "rw_basis_nearest_beta": (I32, [C.POINTER(D), I32, D]),
     "rw_registration_priors": (I32, [P, P, I32, C.POINTER(I32), P, I32, I32, P, P]),
     "rw_solve_unseeded": (I32, [P, P, P, I32, C.POINTER(rw_solve_opts), P, P, P, I32, P,

@@ -23,8 +23,11 @@
 // reading an accumulator.  Warp w reads accumulator lanes 32 (w % 4) .. + 31 with tcgen05.ld,
 // columns 128 (w / 4) .. + 127.
 #include "rw_internal.cuh"
+#include "tc_common.cuh"
 
 #include <algorithm>
+
+using namespace rwtc;
 
 namespace {
 
@@ -39,47 +42,6 @@ constexpr int kBTile = kTN * 128;            // bytes of one K-major B tile
 constexpr int kStage = 2 * kATile + 2 * kBTile;
 constexpr int kSmem = 2 * kStage + 1024 + 64;  // two stages, alignment slack, barriers
 
-__device__ __forceinline__ unsigned smem_addr(const void* p) {
-  return (unsigned)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void mbar_init1(uint64_t* bar) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bar)) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_poll(uint64_t* bar, unsigned parity) {
-  unsigned done;
-  asm volatile(
-      "{\n.reg .pred p;\n"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-      "selp.u32 %0, 1, 0, p;\n}"
-      : "=r"(done)
-      : "r"(smem_addr(bar)), "r"(parity)
-      : "memory");
-  return done != 0;
-}
-
-// Bounded wait: gives up after a fixed number of polls, records RW_DEV_TIMEOUT and reports
-// failure (the caller then skips the remaining work, frees its tensor memory and returns).
-__device__ __forceinline__ bool mbar_wait_limited(uint64_t* bar, unsigned parity, int* status) {
-  for (int it = 0; it <= (1 << 22); ++it)
-    if (mbar_poll(bar, parity)) return true;
-  atomicOr(status, RW_DEV_TIMEOUT);
-  return false;
-}
-
-// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, 8-row groups 1024 bytes
-// apart (stride byte offset), start address in 16-byte units, descriptor version 1.
-__device__ __forceinline__ uint64_t kmajor_sw128_desc(unsigned saddr) {
-  uint64_t d = 0;
-  d |= (uint64_t)((saddr >> 4) & 0x3FFF);
-  d |= (uint64_t)1 << 16;                    // leading byte offset (unused with this swizzle)
-  d |= (uint64_t)(1024 >> 4) << 32;          // stride byte offset
-  d |= (uint64_t)1 << 46;                    // version
-  d |= (uint64_t)2 << 61;                    // 128-byte swizzle
-  return d;
-}
-
 // Instruction descriptor: dense, D = F32, A = B = TF32, both K-major, N = 256, M = 128.
 constexpr uint32_t kIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kTN >> 3) << 17) |
                             ((uint32_t)(kTM >> 4) << 24);
@@ -93,21 +55,8 @@ __device__ __forceinline__ void mma_tf32(uint32_t dtmem, uint64_t adesc, uint64_
       : "memory");
 }
 
-__device__ __forceinline__ void mma_commit(uint64_t* bar) {
-  asm volatile(
-      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-          smem_addr(bar))
-      : "memory");
-}
-
 __device__ __forceinline__ float tf32_hi(float a) {
   return __uint_as_float(__float_as_uint(a) & 0xFFFFE000u);
-}
-
-// Byte offset of the 16-byte chunk j (K elements 4j..4j+3) of row r in a K-major
-// 128-byte-swizzled tile.
-__device__ __forceinline__ int sw128_chunk(int r, int j) {
-  return (r >> 3) * 1024 + (r & 7) * 128 + ((j ^ (r & 7)) << 4);
 }
 
 // Loads rows k0 + 4 j0 .. k0 + 4 (j0 + NJ) - 1 of column `col` (zero outside N x ncols),
@@ -240,9 +189,9 @@ k_gram_tc(const float* __restrict__ A, int64_t lda, const float* __restrict__ B,
       for (int kk = 0; kk < kKB / 8; ++kk) {   // 8 TF32 values = 32 bytes per K-step
         const unsigned o = kk * 32;
         const uint32_t acc0 = (!first || kk > 0) ? 1u : 0u;
-        mma_tf32(d, kmajor_sw128_desc(ahi + o), kmajor_sw128_desc(bhi + o), acc0);
-        mma_tf32(d, kmajor_sw128_desc(ahi + o), kmajor_sw128_desc(blo + o), 1u);
-        mma_tf32(d, kmajor_sw128_desc(alo + o), kmajor_sw128_desc(bhi + o), 1u);
+        mma_tf32(d, kmajor_desc(ahi + o), kmajor_desc(bhi + o), acc0);
+        mma_tf32(d, kmajor_desc(ahi + o), kmajor_desc(blo + o), 1u);
+        mma_tf32(d, kmajor_desc(alo + o), kmajor_desc(bhi + o), 1u);
       }
       mma_commit(&bar[b]);
       if ((s % kGroup) == kGroup - 1 || s == nst - 1) mma_commit(&accbar[g & 1]);

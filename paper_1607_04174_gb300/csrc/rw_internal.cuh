@@ -200,6 +200,22 @@ rw_status rw_copy_cols(const float* src, int64_t lds, float* dst, int64_t ldd, i
                        const int* cols, int ncols, cudaStream_t st);
 rw_status rw_f64_to_f32(const double* a, float* b, int64_t n, cudaStream_t st);
 
+// Tensor-core passes over the 16-bit basis copy (csrc/proj_tc.cu).  rw_project_tc writes the
+// projection partials scaled by kTcProjScale; both take nchunk_max <= 32, lp <= 32.
+constexpr float kTcProjScale = 4096.f;
+template <typename T>
+rw_status rw_project_tc(const T* Qp, int64_t N, int nchunk_max, const float* phat, int lp,
+                        const int* seedlab, const int* mdev, float* part, int nblk, int* status,
+                        cudaStream_t st);
+template <typename T>
+rw_status rw_backproject_tc(const T* Qp, int64_t N, int nchunk_max, const float* C, int lp,
+                            float cscale, const int* seedlab, const float* sq, const float* s,
+                            int L, const int* mdev, float* xhat, float* U, uint8_t* labels,
+                            int* clear, const float* nul, int* status, int nblk, cudaStream_t st);
+// whether a basis pass (which = 1: projection, 2: back-projection) of a 16-bit copy with row
+// pitch ld16 runs on the tensor cores
+bool rw_tc_passes(int ld16, int which);
+
 // Seed bookkeeping shared by the fast solve, the PCG solve and the gradients: resets the label
 // array when needed, scatters the seeds (per-block label statistics) and, unless deferred,
 // launches the priors kernel; launch_priors launches it later (early = 1: other kernels were

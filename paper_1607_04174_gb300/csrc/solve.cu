@@ -26,6 +26,7 @@
 #include <cooperative_groups.h>
 
 #include <algorithm>
+#include <atomic>
 #include <mutex>
 #include <unordered_map>
 #include <cstring>
@@ -2753,6 +2754,12 @@ rw_status launch_proj_back(bool back, const T* Q, int ldq, const float* phat,
   const int cpr = ldq / V;
   if constexpr (V == 8) {  // 16-bit copies: panel-major layout, ldq = 8 x chunks
     const int nchunk = ldq / 8;
+    if (rw_tc_passes(ldq, back ? 2 : 1)) {   // tensor cores (the caller sized nblk and scale)
+      if (!back)
+        return rw_project_tc<T>(Q, g->N, nchunk, phat, LP, seedlab, mdev, part, nblk, g->status, st);
+      return rw_backproject_tc<T>(Q, g->N, nchunk, C, LP, cscale, seedlab, g->sq, g->s, L, mdev,
+                                  xhat, U, labels, clear, nul, g->status, nblk, st);
+    }
     if (!back) {
       const int64_t rpb = (g->N + nblk - 1) / nblk;
       if constexpr (LP <= 8) {
@@ -3091,6 +3098,21 @@ rw_status launch_priors(const rw_graph* g, int L, int prior_mode, const float* p
   return RW_OK;
 }
 
+// The two 16-bit basis passes run on the CUDA cores unless rw_set_tc_passes puts them on the
+// tensor cores (csrc/proj_tc.cu; bit 0: projection, bit 1: back-projection); copies wider than
+// 256 columns keep the CUDA-core kernels.
+namespace {
+std::atomic<int> g_tc_passes{0};
+}
+bool rw_tc_passes(int ld16, int which) {
+  return (g_tc_passes.load(std::memory_order_relaxed) & which) != 0 && ld16 <= 256;
+}
+extern "C" rw_status rw_set_tc_passes(int32_t mask) {
+  if (mask < 0 || mask > 3) return RW_ERR_INVALID_ARG;
+  g_tc_passes.store(mask);
+  return RW_OK;
+}
+
 // Launch shapes of the two 16-bit basis passes (blocks per SM), per graph-size class: entry k
 // applies to graphs with N <= nmax_k (the first such entry, classes ascending).  Set by
 // rw_set_launch_shape from a table the project's autotuner measures; without an entry the
@@ -3250,8 +3272,11 @@ extern "C" rw_status rw_solve(const rw_graph* g, const rw_basis* b, const int32_
   // default: more rows per block, fewer partials to add); the FP32 row kernel 4 per SM
   int proj_per_sm = 2, back_per_sm = 3;
   launch_shape(g->N, &proj_per_sm, &back_per_sm);
-  const int nblk_p = fmt == RW_BASIS_F32 ? nblk : proj_per_sm * sms;
-  float zscale = fmt == RW_BASIS_F16 ? 1.f / b->qscale : 1.f;
+  // the tensor-core passes hold one CTA per SM and write partials scaled by kTcProjScale
+  const bool tc_p = fmt != RW_BASIS_F32 && rw_tc_passes(b->ld16, 1);
+  const bool tc_b = fmt != RW_BASIS_F32 && rw_tc_passes(b->ld16, 2);
+  const int nblk_p = fmt == RW_BASIS_F32 ? nblk : (tc_p ? sms : proj_per_sm * sms);
+  float zscale = (fmt == RW_BASIS_F16 ? 1.f / b->qscale : 1.f) / (tc_p ? kTcProjScale : 1.f);
   float cscale = fmt == RW_BASIS_F16 ? 1.f / b->qscale : 1.f;
   auto project = [&]() -> rw_status {
     if (fmt == RW_BASIS_F16)
@@ -3371,7 +3396,7 @@ extern "C" rw_status rw_solve(const rw_graph* g, const rw_basis* b, const int32_
   if (g0) RW_LAUNCH(k_null_coef, 1, 256, 0, st, C, lp, L, mdev, wv, ginv, nul);
   RW_TRY(mark(5));
   // back-projection (+ refinement); the 16-bit kernel holds three blocks per SM
-  const int nblk_b = fmt == RW_BASIS_F32 ? nblk : back_per_sm * sms;
+  const int nblk_b = fmt == RW_BASIS_F32 ? nblk : (tc_b ? sms : back_per_sm * sms);
   const int steps = opts->refine_steps;
   float* xh0 = nullptr;
   float* xh1 = nullptr;
@@ -3780,9 +3805,12 @@ extern "C" rw_status rw_solve_unseeded(const rw_graph* g, const rw_basis* b,
   launch_shape(N, &proj_per_sm, &back_per_sm);
   if (opts->basis_format == RW_BASIS_F16) {
     const float sc = 1.f / b->qscale;
-    RW_TRY(unseeded_passes<__half>(g, b, b->Q16, b->ld16, sc, sc, priors_dev, K, lp, opts,
+    const bool tc_p = rw_tc_passes(b->ld16, 1), tc_b = rw_tc_passes(b->ld16, 2);
+    RW_TRY(unseeded_passes<__half>(g, b, b->Q16, b->ld16, tc_p ? sc / kTcProjScale : sc, sc,
+                                   priors_dev, K, lp, opts,
                                    prob_dev, st, mall, mdev, Z, lgam, C, Zall, pnorm, gout, part,
-                                   mq, proj_per_sm * sms, back_per_sm * sms));
+                                   mq, tc_p ? sms : proj_per_sm * sms,
+                                   tc_b ? sms : back_per_sm * sms));
   } else {
     RW_TRY(unseeded_passes<float>(g, b, b->Q32, b->ld32, 1.f, 1.f, priors_dev, K, lp, opts,
                                   prob_dev, st, mall, mdev, Z, lgam, C, Zall, pnorm, gout, part,

@@ -105,7 +105,8 @@ def test_null_handles_are_refused_on_the_host(lib):
     before = lib.rw_kernel_launches()
     status_calls = [n for n, (res, _) in abi.PROTOTYPES.items()
                     if res is C.c_int32 and n not in ("rw_basis_m", "rw_set_launch_shape",
-                                                      "rw_basis_nearest_beta")]
+                                                      "rw_basis_nearest_beta",
+                                                      "rw_set_tc_passes")]
     assert len(status_calls) >= 17
     for name in status_calls:
         st = getattr(lib, name)(*_null_args(abi.PROTOTYPES[name][1]))
@@ -116,6 +117,8 @@ def test_null_handles_are_refused_on_the_host(lib):
     assert lib.rw_set_launch_shape(4096, 0, 3) == -1      # a shape out of range
     assert lib.rw_set_launch_shape(4096, 1, 9) == -1
     assert lib.rw_set_launch_shape(0, 1, 1) == 0          # clears the (host-side) table
+    assert lib.rw_set_tc_passes(0) == 0 and lib.rw_set_tc_passes(3) == 0   # host-side switch
+    assert lib.rw_set_tc_passes(4) == -1
     assert lib.rw_basis_nearest_beta(None, 1, 1.0) == -1
     lib.rw_batch_free(None)
     assert lib.rw_block_gram_scratch_bytes(2048, 128, 256) == 256 + 4 * 128 * 256 * 2
@@ -125,7 +128,7 @@ def test_null_handles_are_refused_on_the_host(lib):
     # every declared entry point is one of the calls above or an accessor checked elsewhere
     covered = set(status_calls) | {"rw_basis_m", "rw_graph_num_nodes", "rw_graph_free",
                                    "rw_block_gram_scratch_bytes", "rw_set_launch_shape",
-                                   "rw_basis_nearest_beta",
+                                   "rw_basis_nearest_beta", "rw_set_tc_passes",
                                    "rw_batch_free",
                                    "rw_basis_free", "rw_status_str", "rw_last_error_message",
                                    "rw_kernel_launches"}

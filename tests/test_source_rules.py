@@ -22,13 +22,13 @@ def _strip_comments(text):
 
 
 def test_mbarrier_waits_are_bounded():
-    """The mbarrier polls are mbar_try_wait (solve.cu) and mbar_poll (gram_tc.cu); each has one
-    caller, a bounded loop that gives up (setting a timeout status) after a fixed number of
-    polls."""
+    """The mbarrier polls are mbar_try_wait (solve.cu) and mbar_poll (tc_common.cuh, used by the
+    tensor-core kernels); each has one caller, a bounded loop that gives up (setting a timeout
+    status) after a fixed number of polls."""
     src = {f: _strip_comments(t) for f, t in _sources().items()}
     polls = [f for f, t in src.items() for _ in re.finditer(r"mbarrier\.try_wait", t)]
-    assert sorted(polls) == ["gram_tc.cu", "solve.cu"]
-    g = src["gram_tc.cu"]
+    assert sorted(polls) == ["solve.cu", "tc_common.cuh"]
+    g = src["tc_common.cuh"]
     assert len(re.findall(r"\bmbar_poll\s*\(", g)) == 2
     i = g.index("bool mbar_wait_limited(")
     body = g[i:g.index("\n}\n", i)]
