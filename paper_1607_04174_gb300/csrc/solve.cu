@@ -2741,7 +2741,8 @@ rw_status jacobi(const rw_graph* g, int lp, const float* xin, float* xout, const
   switch (lp) {
     case 4: return launch_jacobi<4>(g, xin, xout, phat, seedlab, L, gamma, omega, last, U, labels, clear, st);
     case 8: return launch_jacobi<8>(g, xin, xout, phat, seedlab, L, gamma, omega, last, U, labels, clear, st);
-    default: return launch_jacobi<16>(g, xin, xout, phat, seedlab, L, gamma, omega, last, U, labels, clear, st);
+    case 16: return launch_jacobi<16>(g, xin, xout, phat, seedlab, L, gamma, omega, last, U, labels, clear, st);
+    default: return launch_jacobi<32>(g, xin, xout, phat, seedlab, L, gamma, omega, last, U, labels, clear, st);
   }
 }
 
@@ -2813,7 +2814,17 @@ rw_status proj_back(int lp, bool back, const T* Q, int ldq, const float* phat, c
   switch (lp) {
     case 4: return launch_proj_back<T, 4>(back, Q, ldq, phat, seedlab, g, mdev, part, nblk, C, cscale, xhat, U, labels, L, clear, nul, st);
     case 8: return launch_proj_back<T, 8>(back, Q, ldq, phat, seedlab, g, mdev, part, nblk, C, cscale, xhat, U, labels, L, clear, nul, st);
-    default: return launch_proj_back<T, 16>(back, Q, ldq, phat, seedlab, g, mdev, part, nblk, C, cscale, xhat, U, labels, L, clear, nul, st);
+    case 16: return launch_proj_back<T, 16>(back, Q, ldq, phat, seedlab, g, mdev, part, nblk, C, cscale, xhat, U, labels, L, clear, nul, st);
+    default:   // 32 labels per pass: the tensor-core kernels only
+      if constexpr (Vec16<T>::V == 8) {
+        if (rw_tc_passes(ldq, back ? 2 : 1)) {
+          if (!back)
+            return rw_project_tc<T>(Q, g->N, ldq / 8, phat, 32, seedlab, mdev, part, nblk, g->status, st);
+          return rw_backproject_tc<T>(Q, g->N, ldq / 8, C, 32, cscale, seedlab, g->sq, g->s, L, mdev,
+                                      xhat, U, labels, clear, nul, g->status, nblk, st);
+        }
+      }
+      return RW_ERR_UNSUPPORTED;
   }
 }
 
@@ -3551,24 +3562,29 @@ namespace {
 
 // P-hat chunk: phat[i][j] = d_i^{1/2} P[i][k0 + j] (j < Lc, zero above); optionally the squared
 // norms of the chunk's P-hat columns, per block in FP64, one atomic per block and label.
+template <int LP>
 __global__ void __launch_bounds__(256)
-k_hat_chunk(const float* __restrict__ P, int K, int k0, int Lc, int lp,
+k_hat_chunk(const float* __restrict__ P, int K, int k0, int Lc,
             const float* __restrict__ sq, int64_t N, float* __restrict__ phat,
             double* __restrict__ pnorm) {
-  __shared__ double red[8][8];
-  double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  __shared__ double red[8][LP];
+  double acc[LP];
+#pragma unroll
+  for (int j = 0; j < LP; ++j) acc[j] = 0.0;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
        i += (int64_t)gridDim.x * blockDim.x) {
     const float s = sq[i];
-    for (int j = 0; j < lp; ++j) {
+#pragma unroll
+    for (int j = 0; j < LP; ++j) {
       const float v = j < Lc ? s * P[i * K + k0 + j] : 0.f;
-      phat[i * lp + j] = v;
+      phat[i * LP + j] = v;
       acc[j] += (double)v * v;
     }
   }
   if (!pnorm) return;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  for (int j = 0; j < 8; ++j) {
+#pragma unroll
+  for (int j = 0; j < LP; ++j) {
     double v = acc[j];
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     if (lane == 0) red[w][j] = v;
@@ -3579,6 +3595,18 @@ k_hat_chunk(const float* __restrict__ P, int K, int k0, int Lc, int lp,
     for (int ww = 0; ww < 8; ++ww) t += red[ww][threadIdx.x];
     atomicAdd(&pnorm[k0 + threadIdx.x], t);
   }
+}
+
+static rw_status hat_chunk(int lp, unsigned nblk, cudaStream_t st, const float* P, int K, int k0,
+                           int Lc, const float* sq, int64_t N, float* phat, double* pnorm) {
+  switch (lp) {
+    case 4: k_hat_chunk<4><<<nblk, 256, 0, st>>>(P, K, k0, Lc, sq, N, phat, pnorm); break;
+    case 8: k_hat_chunk<8><<<nblk, 256, 0, st>>>(P, K, k0, Lc, sq, N, phat, pnorm); break;
+    case 16: k_hat_chunk<16><<<nblk, 256, 0, st>>>(P, K, k0, Lc, sq, N, phat, pnorm); break;
+    default: k_hat_chunk<32><<<nblk, 256, 0, st>>>(P, K, k0, Lc, sq, N, phat, pnorm); break;
+  }
+  RW_LAUNCH_CHECK();
+  return RW_OK;
 }
 
 __global__ void k_store_z(const float* __restrict__ Z, int lp, int Lc, int k0, int rows, int K,
@@ -3699,9 +3727,7 @@ static rw_status unseeded_passes(const rw_graph* g, const rw_basis* b, const T* 
   RW_LAUNCH(k_set_m, 1, 32, 0, st, mall, m_max);
   for (int c = 0; c < nchunks; ++c) {
     const int k0 = c * lp, Lc = std::min(lp, K - k0);
-    k_hat_chunk<<<hblk, 256, 0, st>>>(priors, K, k0, Lc, lp, g->sq, N, phat,
-                                      adaptive ? pnorm : nullptr);
-    RW_LAUNCH_CHECK();
+    RW_TRY(hat_chunk(lp, hblk, st, priors, K, k0, Lc, g->sq, N, phat, adaptive ? pnorm : nullptr));
     RW_TRY(proj_back<T>(lp, false, Q, ldq, phat, seedlab, g, mall, part, nblk_p, nullptr, 0.f,
                         nullptr, nullptr, nullptr, Lc, st));
     RW_LAUNCH(k_reduce_partials, rw_blocks((int64_t)std::max(mq * lp, m_max) * 32, 256), 256, 0,
@@ -3723,8 +3749,7 @@ static rw_status unseeded_passes(const rw_graph* g, const rw_basis* b, const T* 
   float* Uc = ws.reg.as<float>();
   for (int c = 0; c < nchunks; ++c) {
     const int k0 = c * lp, Lc = std::min(lp, K - k0);
-    k_hat_chunk<<<hblk, 256, 0, st>>>(priors, K, k0, Lc, lp, g->sq, N, phat, nullptr);
-    RW_LAUNCH_CHECK();
+    RW_TRY(hat_chunk(lp, hblk, st, priors, K, k0, Lc, g->sq, N, phat, nullptr));
     k_c_unseeded<<<rw_blocks((int64_t)mq * lp, 256), 256, 0, st>>>(Zall, K, k0, Lc, lp, b->lam,
                                                                  gamma, mdev, mq, C);
     RW_LAUNCH_CHECK();
@@ -3766,7 +3791,11 @@ extern "C" rw_status rw_solve_unseeded(const rw_graph* g, const rw_basis* b,
   rw_graph* gm = const_cast<rw_graph*>(g);
   SolveWorkspace& ws = gm->ws;
   const int64_t N = g->N;
-  const int lp = K <= 4 ? 4 : 8;
+  // labels per pass: 8 on the CUDA cores; with both basis passes on the tensor cores up to 32
+  // (one pass over the basis for every 32 labels)
+  const bool tc_all = rw_tc_passes(b->ld16, 1) && rw_tc_passes(b->ld16, 2) &&
+                      opts->basis_format != RW_BASIS_F32;
+  const int lp = K <= 4 ? 4 : (K <= 8 || !tc_all ? 8 : (K <= 16 ? 16 : 32));
   const int sms = g_rw_num_sms;
   const int nblk = 4 * sms;
   const int mq = std::max(b->ld16, b->ld32);

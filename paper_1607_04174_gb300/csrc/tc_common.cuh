@@ -1,6 +1,6 @@
 // Building blocks of the tcgen05 kernels (5th-generation tensor cores, tensor-memory
-// accumulators): shared-memory matrix descriptors for 128-byte-swizzled tiles, MMA issue and
-// commit, tensor-memory loads, bounded mbarrier waits, cp.async copies.
+// accumulators): shared-memory matrix descriptors, MMA issue and commit, tensor-memory loads,
+// bounded mbarrier waits, cp.async and bulk copies.
 //
 // Tile format.  A 128-byte-swizzled tile is a stack of 8-row groups of 1024 bytes; row r of
 // the tile is 128 bytes (64 16-bit or 32 32-bit values), and its 16-byte chunk j sits at
@@ -10,8 +10,13 @@
 //   MN-major when its rows run along K and the 128 bytes along M (or N): the leading byte
 //            offset is the distance between 64-element MN blocks, the stride byte offset the
 //            distance between 8-row K groups (1024 for stacked groups).
-// (The MN-major field assignment was measured: a one-MMA probe with the two fields swapped
-// gives wrong products.)
+// A tile without swizzle is made of 8-row x 16-byte core matrices (128 contiguous bytes: 8
+// rows of 8 16-bit values).  For a K-major operand the leading byte offset is the distance
+// between core matrices adjacent along K and the stride byte offset the distance along M (or
+// N); for an MN-major operand the leading byte offset is the distance along K and the stride
+// byte offset the distance along M (or N).
+// (The field assignments were measured: one-MMA probes with the two fields swapped give wrong
+// products.)
 #pragma once
 
 #include <cstdint>
@@ -41,6 +46,16 @@ __device__ __forceinline__ uint64_t sw128_desc(unsigned saddr, unsigned lbo, uns
 
 __device__ __forceinline__ uint64_t kmajor_desc(unsigned saddr) { return sw128_desc(saddr, 16, 1024); }
 
+// descriptor of a tile without swizzle (core matrices, see above)
+__device__ __forceinline__ uint64_t plain_desc(unsigned saddr, unsigned lbo, unsigned sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFF);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
+  d |= (uint64_t)1 << 46;
+  return d;
+}
+
 // instruction descriptor of kind::f16: D = F32; A, B = F16 (fmt 0) or BF16 (fmt 1);
 // a_mn / b_mn: operand is MN-major
 __host__ __device__ constexpr uint32_t f16_idesc(int M, int N, int fmt, int a_mn, int b_mn) {
@@ -67,6 +82,32 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
 __device__ __forceinline__ void mbar_init1(uint64_t* bar) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bar)) : "memory");
 }
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+// arrives on bar and adds `bytes` to the transaction count it waits for
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+               "r"(bytes)
+               : "memory");
+}
+// bulk copy global -> shared (16-byte aligned addresses, size a multiple of 16), completion
+// counted in bytes on bar
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes,
+                                         uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+      ::"r"(smem_addr(dst)), "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+// arrives on bar once all of this thread's earlier cp.async copies have landed (the barrier's
+// expected count must include this arrival)
+__device__ __forceinline__ void cp_async_arrive_noinc(uint64_t* bar) {
+  asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
 
 __device__ __forceinline__ bool mbar_poll(uint64_t* bar, unsigned parity) {
   unsigned done;
@@ -80,11 +121,16 @@ __device__ __forceinline__ bool mbar_poll(uint64_t* bar, unsigned parity) {
   return done != 0;
 }
 
-// gives up after a fixed number of polls and records RW_DEV_TIMEOUT
-__device__ __forceinline__ bool mbar_wait_limited(uint64_t* bar, unsigned parity, int* status) {
-  for (int it = 0; it <= (1 << 22); ++it)
+// gives up after a fixed number of polls, records RW_DEV_TIMEOUT and raises *abort (when
+// given); also gives up at once when another thread of the block has raised *abort
+__device__ __forceinline__ bool mbar_wait_limited(uint64_t* bar, unsigned parity, int* status,
+                                                  volatile int* abort = nullptr) {
+  for (int it = 0; it <= (1 << 22); ++it) {
     if (mbar_poll(bar, parity)) return true;
+    if (abort && *abort) return false;
+  }
   atomicOr(status, RW_DEV_TIMEOUT);
+  if (abort) *abort = 1;
   return false;
 }
 
