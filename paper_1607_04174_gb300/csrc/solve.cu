@@ -3562,33 +3562,30 @@ namespace {
 
 // P-hat chunk: phat[i][j] = d_i^{1/2} P[i][k0 + j] (j < Lc, zero above); optionally the squared
 // norms of the chunk's P-hat columns, per block in FP64, one atomic per block and label.
+// P-hat rows of one chunk of labels: phat[i][j] = d_i^{1/2} P[i][k0 + j] (zero past Lc), one
+// thread per entry so that both the reads of P and the writes of P-hat are coalesced; with
+// pnorm, also adds ||P-hat column||^2 (per-thread FP64 sums: the grid is a multiple of LP
+// threads, so a thread always meets the same column; warp, then block, then one atomic per
+// column and block).
 template <int LP>
 __global__ void __launch_bounds__(256)
 k_hat_chunk(const float* __restrict__ P, int K, int k0, int Lc,
             const float* __restrict__ sq, int64_t N, float* __restrict__ phat,
             double* __restrict__ pnorm) {
   __shared__ double red[8][LP];
-  double acc[LP];
-#pragma unroll
-  for (int j = 0; j < LP; ++j) acc[j] = 0.0;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const float s = sq[i];
-#pragma unroll
-    for (int j = 0; j < LP; ++j) {
-      const float v = j < Lc ? s * P[i * K + k0 + j] : 0.f;
-      phat[i * LP + j] = v;
-      acc[j] += (double)v * v;
-    }
+  double acc = 0.0;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < N * LP; e += stride) {
+    const int64_t i = e / LP;
+    const int j = (int)(e % LP);
+    const float v = j < Lc ? __ldg(sq + i) * __ldg(P + i * K + k0 + j) : 0.f;
+    phat[e] = v;
+    acc += (double)v * v;
   }
   if (!pnorm) return;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-#pragma unroll
-  for (int j = 0; j < LP; ++j) {
-    double v = acc[j];
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if (lane == 0) red[w][j] = v;
-  }
+  for (int o = 16; o >= LP; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane < LP) red[w][lane] = acc;
   __syncthreads();
   if (threadIdx.x < Lc) {
     double t = 0.0;
@@ -3749,7 +3746,8 @@ static rw_status unseeded_passes(const rw_graph* g, const rw_basis* b, const T* 
   float* Uc = ws.reg.as<float>();
   for (int c = 0; c < nchunks; ++c) {
     const int k0 = c * lp, Lc = std::min(lp, K - k0);
-    RW_TRY(hat_chunk(lp, hblk, st, priors, K, k0, Lc, g->sq, N, phat, nullptr));
+    if (nchunks > 1)   // with one chunk the P-hat rows of the first loop are still in place
+      RW_TRY(hat_chunk(lp, hblk, st, priors, K, k0, Lc, g->sq, N, phat, nullptr));
     k_c_unseeded<<<rw_blocks((int64_t)mq * lp, 256), 256, 0, st>>>(Zall, K, k0, Lc, lp, b->lam,
                                                                  gamma, mdev, mq, C);
     RW_LAUNCH_CHECK();
