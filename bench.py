@@ -1064,9 +1064,9 @@ def main():
     ap.add_argument("--no-stencil", action="store_true", help="skip the stencil block")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-serving block")
     ap.add_argument("--no-gamma0", action="store_true", help="skip the gamma = 0 block")
-    ap.add_argument("--tc-passes", type=int, default=0, choices=[0, 1, 2, 3],
+    ap.add_argument("--tc-passes", type=int, default=4, choices=[0, 1, 2, 3, 4],
                     help="basis passes on the tensor cores: bit 0 projection, bit 1 "
-                         "back-projection (default 0: both on CUDA cores)")
+                         "back-projection, 4 (default): both for passes of more than 8 labels")
     ap.add_argument("--no-registration", action="store_true",
                     help="skip the 96^3 registration block")
     ap.add_argument("--registration-only", action="store_true",

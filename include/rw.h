@@ -425,11 +425,13 @@ rw_status rw_rayleigh_quotients_noalloc(const rw_graph* g, const float* Q_dev, i
  * [1, 8].  The project's autotuner (paper_1607_04174_gb300/autotune.py) measures the table.
  * rw_set_tc_passes selects, process-wide, the tensor-core kernels or the CUDA-core kernels for
  * the two passes over a 16-bit basis copy in rw_solve, rw_solve_unseeded and the batch calls:
- * bit 0 of mask = the projection Z = Q_n^T P_n, bit 1 = the back-projection U_n = Q_n C
- * (Eq. U_lin_comb); 0 (both on CUDA cores) is the default, 3 puts both on tensor cores; other
- * values return RW_ERR_INVALID_ARG.  The launch-shape table applies to the CUDA-core kernels
- * only (the tensor-core ones run one block per SM).  Copies wider than 256 columns and the FP32
- * basis always use the CUDA-core kernels.  Takes effect for launches after the call.
+ * mask bit 0 = the projection Z = Q_n^T P_n on tensor cores, bit 1 = the back-projection
+ * U_n = Q_n C (Eq. U_lin_comb), 4 (the default) = both on tensor cores for passes that carry
+ * more than 8 labels (there rw_solve_unseeded takes up to 32 labels per pass), CUDA cores
+ * otherwise; 0 = always CUDA cores, 3 = always tensor cores; other values return
+ * RW_ERR_INVALID_ARG.  The launch-shape table applies to the CUDA-core kernels only (the
+ * tensor-core ones run one block per SM).  Copies wider than 256 columns and the FP32 basis
+ * always use the CUDA-core kernels.  Takes effect for launches after the call.
  * ---------------------------------------------------------------------------------------- */
 typedef struct rw_batch rw_batch;
 typedef struct rw_batch_item {

@@ -379,8 +379,8 @@ def rw_set_launch_shape(n_max, proj_per_sm, back_per_sm):
 
 
 def rw_set_tc_passes(mask):
-    """bit 0: projection on the tensor cores, bit 1: back-projection (0 = both on CUDA cores,
-    the default; 3 = both on tensor cores)."""
+    """bit 0: projection on the tensor cores, bit 1: back-projection; 4 (the default): both on
+    the tensor cores for passes of more than 8 labels; 0: CUDA cores; 3: tensor cores."""
     return _check(abi.lib().rw_set_tc_passes(int(mask)), "rw_set_tc_passes")
 
 

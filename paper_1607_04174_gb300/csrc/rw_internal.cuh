@@ -213,8 +213,8 @@ rw_status rw_backproject_tc(const T* Qp, int64_t N, int nchunk_max, const float*
                             int L, const int* mdev, float* xhat, float* U, uint8_t* labels,
                             int* clear, const float* nul, int* status, int nblk, cudaStream_t st);
 // whether a basis pass (which = 1: projection, 2: back-projection) of a 16-bit copy with row
-// pitch ld16 runs on the tensor cores
-bool rw_tc_passes(int ld16, int which);
+// pitch ld16 carrying lp padded labels runs on the tensor cores
+bool rw_tc_passes(int ld16, int which, int lp);
 
 // Seed bookkeeping shared by the fast solve, the PCG solve and the gradients: resets the label
 // array when needed, scatters the seeds (per-block label statistics) and, unless deferred,

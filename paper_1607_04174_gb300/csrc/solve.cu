@@ -2717,10 +2717,68 @@ k_jacobi_grid(const float* __restrict__ xin, float* __restrict__ xout,
   if (clear_seedlab && sl >= 0) clear_seedlab[i] = -1;  // the label array is all -1 again for the next call
 }
 
+// A non-final damped-Jacobi step for wide rows (LP >= 16 labels) on a grid graph: one thread
+// per (voxel, 4-label chunk), so that the row loads of a warp are contiguous; the neighbour
+// terms are added in the order of k_jacobi_grid (same result).
+template <int LP>
+__global__ void __launch_bounds__(256)
+k_jacobi_wide(const float* __restrict__ xin, float* __restrict__ xout,
+              const float* __restrict__ phat, const int* __restrict__ seedlab,
+              const float* __restrict__ cw, const float* __restrict__ d, int normalized,
+              int ndim, int DX, int DY, int DZ, int64_t N, float gamma, float omega) {
+  rw_grid_wait();
+  rw_grid_trigger();
+  constexpr int NV = LP / 4;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= DX * NV) return;
+  const int x = t / NV, c = t % NV;
+  const int y = blockIdx.y, z = blockIdx.z;
+  const int64_t sy = DX, sz = (int64_t)DX * DY;
+  const int64_t i = x + sy * y + sz * z;
+  const float4* x4 = reinterpret_cast<const float4*>(xin);
+  const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+  const bool hx0 = x > 0, hx1 = x + 1 < DX, hy0 = y > 0, hy1 = y + 1 < DY;
+  const bool hz0 = ndim == 3 && z > 0, hz1 = ndim == 3 && z + 1 < DZ;
+  const float4 xo = x4[i * NV + c];
+  const float4 v0 = hx0 ? x4[(i - 1) * NV + c] : zero, v1 = hx1 ? x4[(i + 1) * NV + c] : zero;
+  const float4 v2 = hy0 ? x4[(i - sy) * NV + c] : zero, v3 = hy1 ? x4[(i + sy) * NV + c] : zero;
+  const float4 v4 = hz0 ? x4[(i - sz) * NV + c] : zero, v5 = hz1 ? x4[(i + sz) * NV + c] : zero;
+  const float c0 = hx0 ? cw[i - 1] : 0.f, c1 = hx1 ? cw[i] : 0.f;
+  const float c2 = hy0 ? cw[N + i - sy] : 0.f, c3 = hy1 ? cw[N + i] : 0.f;
+  const float c4 = hz0 ? cw[2 * N + i - sz] : 0.f, c5 = hz1 ? cw[2 * N + i] : 0.f;
+  const float4 pv = reinterpret_cast<const float4*>(phat)[i * NV + c];
+  const int sl = seedlab[i];
+  const float aii = (normalized ? 1.f : d[i]) + gamma;
+  float4 acc = zero;
+  auto add = [&](bool h, float cc, float4 v) {
+    if (!h) return;
+    acc.x = fmaf(cc, v.x, acc.x); acc.y = fmaf(cc, v.y, acc.y);
+    acc.z = fmaf(cc, v.z, acc.z); acc.w = fmaf(cc, v.w, acc.w);
+  };
+  add(hx0, c0, v0); add(hx1, c1, v1); add(hy0, c2, v2); add(hy1, c3, v3);
+  add(hz0, c4, v4); add(hz1, c5, v5);
+  float4 o = xo;
+  if (sl < 0) {
+    const float f = omega / aii, keep = 1.f - omega;
+    o.x = keep * xo.x + f * fmaf(gamma, pv.x, acc.x);
+    o.y = keep * xo.y + f * fmaf(gamma, pv.y, acc.y);
+    o.z = keep * xo.z + f * fmaf(gamma, pv.z, acc.z);
+    o.w = keep * xo.w + f * fmaf(gamma, pv.w, acc.w);
+  }
+  reinterpret_cast<float4*>(xout)[i * NV + c] = o;
+}
+
 template <int LP>
 rw_status launch_jacobi(const rw_graph* g, const float* xin, float* xout, const float* phat,
                         const int* seedlab, int L, float gamma, float omega, int last,
                         float* U, uint8_t* labels, int* clear, cudaStream_t st) {
+  if (g->kind == RW_GRAPH_GRID && LP >= 16 && !last) {
+    const dim3 grid((unsigned)((g->dims[0] * (LP / 4) + 255) / 256), (unsigned)g->dims[1],
+                    (unsigned)g->dims[2]);
+    RW_LAUNCH((k_jacobi_wide<LP>), grid, 256, 0, st, xin, xout, phat, seedlab, g->cw, g->d,
+              g->normalized, g->ndim, g->dims[0], g->dims[1], g->dims[2], g->N, gamma, omega);
+    return RW_OK;
+  }
   if (g->kind == RW_GRAPH_GRID) {
     const dim3 grid((unsigned)((g->dims[0] + 127) / 128), (unsigned)g->dims[1], (unsigned)g->dims[2]);
     RW_LAUNCH((k_jacobi_grid<LP>), grid, 128, 0, st, xin, xout, phat, seedlab, g->cw, g->d, g->s,
@@ -2755,7 +2813,7 @@ rw_status launch_proj_back(bool back, const T* Q, int ldq, const float* phat,
   const int cpr = ldq / V;
   if constexpr (V == 8) {  // 16-bit copies: panel-major layout, ldq = 8 x chunks
     const int nchunk = ldq / 8;
-    if (rw_tc_passes(ldq, back ? 2 : 1)) {   // tensor cores (the caller sized nblk and scale)
+    if (rw_tc_passes(ldq, back ? 2 : 1, LP)) {   // tensor cores (the caller sized nblk, scale)
       if (!back)
         return rw_project_tc<T>(Q, g->N, nchunk, phat, LP, seedlab, mdev, part, nblk, g->status, st);
       return rw_backproject_tc<T>(Q, g->N, nchunk, C, LP, cscale, seedlab, g->sq, g->s, L, mdev,
@@ -2817,7 +2875,7 @@ rw_status proj_back(int lp, bool back, const T* Q, int ldq, const float* phat, c
     case 16: return launch_proj_back<T, 16>(back, Q, ldq, phat, seedlab, g, mdev, part, nblk, C, cscale, xhat, U, labels, L, clear, nul, st);
     default:   // 32 labels per pass: the tensor-core kernels only
       if constexpr (Vec16<T>::V == 8) {
-        if (rw_tc_passes(ldq, back ? 2 : 1)) {
+        if (rw_tc_passes(ldq, back ? 2 : 1, 32)) {
           if (!back)
             return rw_project_tc<T>(Q, g->N, ldq / 8, phat, 32, seedlab, mdev, part, nblk, g->status, st);
           return rw_backproject_tc<T>(Q, g->N, ldq / 8, C, 32, cscale, seedlab, g->sq, g->s, L, mdev,
@@ -3109,17 +3167,18 @@ rw_status launch_priors(const rw_graph* g, int L, int prior_mode, const float* p
   return RW_OK;
 }
 
-// The two 16-bit basis passes run on the CUDA cores unless rw_set_tc_passes puts them on the
-// tensor cores (csrc/proj_tc.cu; bit 0: projection, bit 1: back-projection); copies wider than
-// 256 columns keep the CUDA-core kernels.
+// Which 16-bit basis passes run on the tensor cores (csrc/proj_tc.cu), set by rw_set_tc_passes:
+// bit 0 the projection, bit 1 the back-projection, bit 2 (the default) both for passes that
+// carry 16 or more padded labels; copies wider than 256 columns keep the CUDA-core kernels.
 namespace {
-std::atomic<int> g_tc_passes{0};
+std::atomic<int> g_tc_passes{4};
 }
-bool rw_tc_passes(int ld16, int which) {
-  return (g_tc_passes.load(std::memory_order_relaxed) & which) != 0 && ld16 <= 256;
+bool rw_tc_passes(int ld16, int which, int lp) {
+  const int mode = g_tc_passes.load(std::memory_order_relaxed);
+  return ld16 <= 256 && ((mode & which) != 0 || ((mode & 4) != 0 && lp >= 16));
 }
 extern "C" rw_status rw_set_tc_passes(int32_t mask) {
-  if (mask < 0 || mask > 3) return RW_ERR_INVALID_ARG;
+  if (mask < 0 || mask > 4) return RW_ERR_INVALID_ARG;
   g_tc_passes.store(mask);
   return RW_OK;
 }
@@ -3284,8 +3343,8 @@ extern "C" rw_status rw_solve(const rw_graph* g, const rw_basis* b, const int32_
   int proj_per_sm = 2, back_per_sm = 3;
   launch_shape(g->N, &proj_per_sm, &back_per_sm);
   // the tensor-core passes hold one CTA per SM and write partials scaled by kTcProjScale
-  const bool tc_p = fmt != RW_BASIS_F32 && rw_tc_passes(b->ld16, 1);
-  const bool tc_b = fmt != RW_BASIS_F32 && rw_tc_passes(b->ld16, 2);
+  const bool tc_p = fmt != RW_BASIS_F32 && rw_tc_passes(b->ld16, 1, lp);
+  const bool tc_b = fmt != RW_BASIS_F32 && rw_tc_passes(b->ld16, 2, lp);
   const int nblk_p = fmt == RW_BASIS_F32 ? nblk : (tc_p ? sms : proj_per_sm * sms);
   float zscale = (fmt == RW_BASIS_F16 ? 1.f / b->qscale : 1.f) / (tc_p ? kTcProjScale : 1.f);
   float cscale = fmt == RW_BASIS_F16 ? 1.f / b->qscale : 1.f;
@@ -3791,7 +3850,7 @@ extern "C" rw_status rw_solve_unseeded(const rw_graph* g, const rw_basis* b,
   const int64_t N = g->N;
   // labels per pass: 8 on the CUDA cores; with both basis passes on the tensor cores up to 32
   // (one pass over the basis for every 32 labels)
-  const bool tc_all = rw_tc_passes(b->ld16, 1) && rw_tc_passes(b->ld16, 2) &&
+  const bool tc_all = rw_tc_passes(b->ld16, 1, 32) && rw_tc_passes(b->ld16, 2, 32) &&
                       opts->basis_format != RW_BASIS_F32;
   const int lp = K <= 4 ? 4 : (K <= 8 || !tc_all ? 8 : (K <= 16 ? 16 : 32));
   const int sms = g_rw_num_sms;
@@ -3832,7 +3891,7 @@ extern "C" rw_status rw_solve_unseeded(const rw_graph* g, const rw_basis* b,
   launch_shape(N, &proj_per_sm, &back_per_sm);
   if (opts->basis_format == RW_BASIS_F16) {
     const float sc = 1.f / b->qscale;
-    const bool tc_p = rw_tc_passes(b->ld16, 1), tc_b = rw_tc_passes(b->ld16, 2);
+    const bool tc_p = rw_tc_passes(b->ld16, 1, lp), tc_b = rw_tc_passes(b->ld16, 2, lp);
     RW_TRY(unseeded_passes<__half>(g, b, b->Q16, b->ld16, tc_p ? sc / kTcProjScale : sc, sc,
                                    priors_dev, K, lp, opts,
                                    prob_dev, st, mall, mdev, Z, lgam, C, Zall, pnorm, gout, part,

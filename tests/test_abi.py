@@ -118,7 +118,7 @@ def test_null_handles_are_refused_on_the_host(lib):
     assert lib.rw_set_launch_shape(4096, 1, 9) == -1
     assert lib.rw_set_launch_shape(0, 1, 1) == 0          # clears the (host-side) table
     assert lib.rw_set_tc_passes(0) == 0 and lib.rw_set_tc_passes(3) == 0   # host-side switch
-    assert lib.rw_set_tc_passes(4) == -1
+    assert lib.rw_set_tc_passes(5) == -1 and lib.rw_set_tc_passes(4) == 0
     assert lib.rw_basis_nearest_beta(None, 1, 1.0) == -1
     lib.rw_batch_free(None)
     assert lib.rw_block_gram_scratch_bytes(2048, 128, 256) == 256 + 4 * 128 * 256 * 2

@@ -24,7 +24,7 @@ def _built():
     from paper_1607_04174_gb300 import build
     build.build()
     yield
-    rw.rw_set_tc_passes(0)
+    rw.rw_set_tc_passes(4)
 
 
 def _both(case, n_labels, **kw):
@@ -40,7 +40,7 @@ def _both(case, n_labels, **kw):
                                   to_dev(case["sl"].astype(np.int32)), n_labels, prob, lab, **kw)
             out.append((prob.cpu().numpy().astype(np.float64), lab.cpu().numpy(), info))
     finally:
-        rw.rw_set_tc_passes(0)
+        rw.rw_set_tc_passes(4)
         rw.rw_basis_free(b)
         rw.rw_graph_free(g)
     return out
@@ -108,7 +108,7 @@ def test_unseeded_registration_solve():
                                           m_step=10, eps=0.1, refine_steps=3)
             out.append((prob.cpu().numpy().astype(np.float64), m_used))
     finally:
-        rw.rw_set_tc_passes(0)
+        rw.rw_set_tc_passes(4)
         rw.rw_basis_free(b)
         rw.rw_graph_free(g)
     (Ut, mt), (Uc, mc) = out
@@ -141,7 +141,7 @@ def test_wide_basis_each_pass_alone(m):
                         gamma=1e-3, m=m, refine_steps=0)
             res[mask] = prob.cpu().numpy().astype(np.float64)
     finally:
-        rw.rw_set_tc_passes(0)
+        rw.rw_set_tc_passes(4)
         rw.rw_basis_free(b)
         rw.rw_graph_free(g)
     for mask in (1, 2, 3):
