@@ -8,33 +8,42 @@
 // grid extended by h voxels on every side (so the clamping of each patch voxel is exactly the
 // definition's), computed as one pass per axis of 2 h + 1 taps.  Every buffer is voxel-major
 // with the K labels interleaved (label fastest), so each pass reads and writes coalesced:
-//   k_reg_absdiff: A on the extended grid;
-//   k_reg_box:     the sum along one axis, shrinking that axis back to the image;
-//   k_reg_normalize: one thread per voxel, log-sum-exp shift by the smallest squared sum.
+//   k_reg_absdiff_x: A summed along x, computed from F and M on the fly (the extended grid
+//                    shrunk back to the image along x);
+//   k_reg_box:       the sum along the middle axis (3-D: y);
+//   k_reg_box_norm:  the sum along the last axis and the normalization, 32 voxels per block:
+//                    the sums go through shared memory and one thread per voxel takes the
+//                    log-sum-exp shift by the smallest squared sum.
+// The sums are taken in the same order as the definition's passes (A, then x, y, z).
 #include "rw_internal.cuh"
 
 namespace {
 
 __device__ __forceinline__ int clampi(int v, int n) { return v < 0 ? 0 : (v >= n ? n - 1 : v); }
 
-// A[((ze * EY + ye) * EX + xe) * K + k], extended coordinates xe = x + h, ...
+// B[((ze * EY + ye) * DX + x) * K + k] = sum over t in [0, 2h] of A_k at extended (x + t, ye, ze),
+// i.e. of |F - M(. + d_k)| at image coordinates (x + t - h, ye - h, ze - h), clamped
 __global__ void __launch_bounds__(256)
-k_reg_absdiff(const float* __restrict__ F, const float* __restrict__ M, int ndim, int DX, int DY,
-              int DZ, const int32_t* __restrict__ disp, int K, int h, int EX, int EY, int EZ,
-              float* __restrict__ A) {
+k_reg_absdiff_x(const float* __restrict__ F, const float* __restrict__ M, int ndim, int DX,
+                int DY, int DZ, const int32_t* __restrict__ disp, int K, int h, int EY, int EZ,
+                float* __restrict__ B) {
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t total = (int64_t)EX * EY * EZ * K;
+  const int64_t total = (int64_t)DX * EY * EZ * K;
   if (e >= total) return;
   const int64_t v = e / K;
   const int k = (int)(e - v * K);
-  const int xe = (int)(v % EX), ye = (int)((v / EX) % EY), ze = (int)(v / ((int64_t)EX * EY));
-  const int x = xe - h, y = ye - (EY > DY ? h : 0), z = ze - (EZ > DZ ? h : 0);
+  const int x0 = (int)(v % DX), ye = (int)((v / DX) % EY), ze = (int)(v / ((int64_t)DX * EY));
+  const int y = ye - (EY > DY ? h : 0), z = ze - (EZ > DZ ? h : 0);
   const int dx = disp[k * ndim + 0], dy = disp[k * ndim + 1];
   const int dz = ndim == 3 ? disp[k * ndim + 2] : 0;
-  const float fv = __ldg(F + ((int64_t)clampi(z, DZ) * DY + clampi(y, DY)) * DX + clampi(x, DX));
-  const float mv = __ldg(M + ((int64_t)clampi(z + dz, DZ) * DY + clampi(y + dy, DY)) * DX +
-                         clampi(x + dx, DX));
-  A[e] = fabsf(fv - mv);
+  const float* Fr = F + ((int64_t)clampi(z, DZ) * DY + clampi(y, DY)) * DX;
+  const float* Mr = M + ((int64_t)clampi(z + dz, DZ) * DY + clampi(y + dy, DY)) * DX;
+  float sum = 0.f;
+  for (int t = 0; t <= 2 * h; ++t) {
+    const int x = x0 + t - h;
+    sum += fabsf(__ldg(Fr + clampi(x, DX)) - __ldg(Mr + clampi(x + dx, DX)));
+  }
+  B[e] = sum;
 }
 
 // out[(z, y, x) in the output box][k] = sum over t in [0, 2h] of in[(z, y, x) + t along axis][k],
@@ -55,21 +64,43 @@ k_reg_box(const float* __restrict__ in, int IX, int IY, int axis, int h, int OX,
   out[e] = s;
 }
 
+// the box sum along `axis` (as k_reg_box, output extent (OX, OY, OZ) = the image) and the
+// priors: for the 32 voxels of a block, P_k = exp(lo - s_k^2) / sum_j exp(lo - s_j^2) with
+// lo = min_k s_k^2; the block's sums and priors are contiguous, read and written coalesced
+constexpr int kNormVox = 32;
+
 __global__ void __launch_bounds__(256)
-k_reg_normalize(float* __restrict__ P, int K, int64_t N) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= N) return;
-  float* p = P + i * K;
-  float lo = INFINITY;
-  for (int k = 0; k < K; ++k) lo = fminf(lo, p[k] * p[k]);
-  float sum = 0.f;
-  for (int k = 0; k < K; ++k) {
-    const float v = expf(lo - p[k] * p[k]);
-    p[k] = v;
-    sum += v;
+k_reg_box_norm(const float* __restrict__ in, int IX, int IY, int axis, int h, int OX, int OY,
+               int64_t N, int K, float* __restrict__ P) {
+  extern __shared__ float sbuf[];   // kNormVox x K sums
+  const int64_t v0 = (int64_t)blockIdx.x * kNormVox;
+  const int nv = (int)(N - v0 < kNormVox ? N - v0 : kNormVox);
+  const int64_t step = (axis == 0 ? 1 : (axis == 1 ? (int64_t)IX : (int64_t)IX * IY)) * K;
+  for (int e = threadIdx.x; e < nv * K; e += blockDim.x) {
+    const int64_t v = v0 + e / K;
+    const int k = e % K;
+    const int x = (int)(v % OX), y = (int)((v / OX) % OY), z = (int)(v / ((int64_t)OX * OY));
+    const int64_t base = (((int64_t)z * IY + y) * IX + x) * K + k;
+    float s = 0.f;
+    for (int t = 0; t <= 2 * h; ++t) s += __ldg(in + base + t * step);
+    sbuf[e] = s;
   }
-  const float inv = 1.f / sum;
-  for (int k = 0; k < K; ++k) p[k] *= inv;
+  __syncthreads();
+  if (threadIdx.x < nv) {
+    float* p = sbuf + threadIdx.x * K;
+    float lo = INFINITY;
+    for (int k = 0; k < K; ++k) lo = fminf(lo, p[k] * p[k]);
+    float sum = 0.f;
+    for (int k = 0; k < K; ++k) {
+      const float v = expf(lo - p[k] * p[k]);
+      p[k] = v;
+      sum += v;
+    }
+    const float inv = 1.f / sum;
+    for (int k = 0; k < K; ++k) p[k] *= inv;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < nv * K; e += blockDim.x) P[v0 * K + e] = sbuf[e];
 }
 
 }  // namespace
@@ -86,31 +117,32 @@ extern "C" rw_status rw_registration_priors(const float* fixed_dev, const float*
   const int64_t N = (int64_t)DX * DY * DZ;
   if (N * K > ((int64_t)1 << 40)) return RW_ERR_INVALID_ARG;
   cudaStream_t st = rw_stream(stream);
-  const int EX = DX + 2 * half, EY = DY + 2 * half, EZ = ndim == 3 ? DZ + 2 * half : 1;
-  const int64_t ext = (int64_t)EX * EY * EZ * K;
-  // the two intermediate volumes: stream-ordered allocation, freed behind the last pass
+  const int EY = DY + 2 * half, EZ = ndim == 3 ? DZ + 2 * half : 1;
+  const size_t norm_shm = sizeof(float) * kNormVox * (size_t)K;
+  if (norm_shm > 200 * 1024) return RW_ERR_UNSUPPORTED;
+  // the intermediate volumes: stream-ordered allocation, freed behind the last pass
+  const int64_t nb = (int64_t)DX * EY * EZ * K, nc = ndim == 3 ? (int64_t)DX * DY * EZ * K : 0;
   void* scratch = nullptr;
-  RW_CHECK_CUDA(cudaMallocAsync(&scratch, 2 * sizeof(float) * (size_t)ext, st));
-  float* A = static_cast<float*>(scratch);
-  float* B = A + ext;
-  k_reg_absdiff<<<rw_blocks(ext, 256), 256, 0, st>>>(fixed_dev, moving_dev, ndim, DX, DY, DZ,
-                                                     disp_dev, K, half, EX, EY, EZ, A);
+  RW_CHECK_CUDA(cudaMallocAsync(&scratch, sizeof(float) * (size_t)(nb + nc), st));
+  float* B = static_cast<float*>(scratch);
+  float* C = B + nb;
+  // x (fused with the differences): -> (DX, EY, EZ); 3-D y: -> (DX, DY, EZ); last axis with the
+  // normalization: -> (DX, DY, DZ)
+  k_reg_absdiff_x<<<rw_blocks(nb, 256), 256, 0, st>>>(fixed_dev, moving_dev, ndim, DX, DY, DZ,
+                                                      disp_dev, K, half, EY, EZ, B);
   RW_LAUNCH_CHECK();
-  // x: (EX, EY, EZ) -> (DX, EY, EZ); y: -> (DX, DY, EZ); z (3-D): -> (DX, DY, DZ)
-  k_reg_box<<<rw_blocks((int64_t)DX * EY * EZ * K, 256), 256, 0, st>>>(A, EX, EY, 0, half, DX, EY,
-                                                                       EZ, K, B);
-  RW_LAUNCH_CHECK();
-  float* ylast = ndim == 3 ? A : priors_dev;
-  k_reg_box<<<rw_blocks((int64_t)DX * DY * EZ * K, 256), 256, 0, st>>>(B, DX, EY, 1, half, DX, DY,
-                                                                       EZ, K, ylast);
-  RW_LAUNCH_CHECK();
+  if (norm_shm > 48 * 1024)
+    RW_CHECK_CUDA(cudaFuncSetAttribute(k_reg_box_norm, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)norm_shm));
+  const unsigned nblk = (unsigned)((N + kNormVox - 1) / kNormVox);
   if (ndim == 3) {
-    k_reg_box<<<rw_blocks((int64_t)DX * DY * DZ * K, 256), 256, 0, st>>>(A, DX, DY, 2, half, DX,
-                                                                         DY, DZ, K, priors_dev);
+    k_reg_box<<<rw_blocks(nc, 256), 256, 0, st>>>(B, DX, EY, 1, half, DX, DY, EZ, K, C);
     RW_LAUNCH_CHECK();
+    k_reg_box_norm<<<nblk, 256, norm_shm, st>>>(C, DX, DY, 2, half, DX, DY, N, K, priors_dev);
+  } else {
+    k_reg_box_norm<<<nblk, 256, norm_shm, st>>>(B, DX, EY, 1, half, DX, DY, N, K, priors_dev);
   }
-  RW_CHECK_CUDA(cudaFreeAsync(scratch, st));
-  k_reg_normalize<<<rw_blocks(N, 256), 256, 0, st>>>(priors_dev, K, N);
   RW_LAUNCH_CHECK();
+  RW_CHECK_CUDA(cudaFreeAsync(scratch, st));
   return RW_OK;
 }

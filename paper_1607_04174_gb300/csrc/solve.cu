@@ -2717,15 +2717,17 @@ k_jacobi_grid(const float* __restrict__ xin, float* __restrict__ xout,
   if (clear_seedlab && sl >= 0) clear_seedlab[i] = -1;  // the label array is all -1 again for the next call
 }
 
-// A non-final damped-Jacobi step for wide rows (LP >= 16 labels) on a grid graph: one thread
-// per (voxel, 4-label chunk), so that the row loads of a warp are contiguous; the neighbour
-// terms are added in the order of k_jacobi_grid (same result).
+// A damped-Jacobi step for wide rows (LP >= 16 labels) on a grid graph: one thread per (voxel,
+// 4-label chunk), so that the row loads of a warp are contiguous; the neighbour terms are added
+// in the order of k_jacobi_grid (same result).  The last step writes U = s * x (seeds one-hot)
+// for the first L labels; it does not form the hard labels (a row spans several threads).
 template <int LP>
 __global__ void __launch_bounds__(256)
 k_jacobi_wide(const float* __restrict__ xin, float* __restrict__ xout,
               const float* __restrict__ phat, const int* __restrict__ seedlab,
-              const float* __restrict__ cw, const float* __restrict__ d, int normalized,
-              int ndim, int DX, int DY, int DZ, int64_t N, float gamma, float omega) {
+              const float* __restrict__ cw, const float* __restrict__ d,
+              const float* __restrict__ s, int normalized, int ndim, int DX, int DY, int DZ,
+              int64_t N, float gamma, float omega, int L, float* __restrict__ U) {
   rw_grid_wait();
   rw_grid_trigger();
   constexpr int NV = LP / 4;
@@ -2765,18 +2767,29 @@ k_jacobi_wide(const float* __restrict__ xin, float* __restrict__ xout,
     o.z = keep * xo.z + f * fmaf(gamma, pv.z, acc.z);
     o.w = keep * xo.w + f * fmaf(gamma, pv.w, acc.w);
   }
-  reinterpret_cast<float4*>(xout)[i * NV + c] = o;
+  if (!U) {
+    reinterpret_cast<float4*>(xout)[i * NV + c] = o;
+    return;
+  }
+  const float si = s[i];
+  const float ov[4] = {o.x, o.y, o.z, o.w};
+#pragma unroll
+  for (int t = 0; t < 4; ++t) {
+    const int k = 4 * c + t;
+    if (k < L) U[i * L + k] = (sl >= 0) ? (k == sl ? 1.f : 0.f) : ov[t] * si;
+  }
 }
 
 template <int LP>
 rw_status launch_jacobi(const rw_graph* g, const float* xin, float* xout, const float* phat,
                         const int* seedlab, int L, float gamma, float omega, int last,
                         float* U, uint8_t* labels, int* clear, cudaStream_t st) {
-  if (g->kind == RW_GRAPH_GRID && LP >= 16 && !last) {
+  if (g->kind == RW_GRAPH_GRID && LP >= 16 && (!last || (!labels && !clear))) {
     const dim3 grid((unsigned)((g->dims[0] * (LP / 4) + 255) / 256), (unsigned)g->dims[1],
                     (unsigned)g->dims[2]);
-    RW_LAUNCH((k_jacobi_wide<LP>), grid, 256, 0, st, xin, xout, phat, seedlab, g->cw, g->d,
-              g->normalized, g->ndim, g->dims[0], g->dims[1], g->dims[2], g->N, gamma, omega);
+    RW_LAUNCH((k_jacobi_wide<LP>), grid, 256, 0, st, xin, xout, phat, seedlab, g->cw, g->d, g->s,
+              g->normalized, g->ndim, g->dims[0], g->dims[1], g->dims[2], g->N, gamma, omega, L,
+              last ? U : nullptr);
     return RW_OK;
   }
   if (g->kind == RW_GRAPH_GRID) {
@@ -3802,7 +3815,8 @@ static rw_status unseeded_passes(const rw_graph* g, const rw_basis* b, const T* 
   }
   float* xh0 = steps > 0 ? ws.xhat[0].as<float>() : nullptr;
   float* xh1 = steps > 0 ? ws.xhat[1].as<float>() : nullptr;
-  float* Uc = ws.reg.as<float>();
+  // one chunk holding every label writes prob directly (same layout); else a chunk buffer
+  float* Uc = nchunks == 1 ? prob : ws.reg.as<float>();
   for (int c = 0; c < nchunks; ++c) {
     const int k0 = c * lp, Lc = std::min(lp, K - k0);
     if (nchunks > 1)   // with one chunk the P-hat rows of the first loop are still in place
@@ -3822,8 +3836,10 @@ static rw_status unseeded_passes(const rw_graph* g, const rw_basis* b, const T* 
         std::swap(a, o);
       }
     }
-    k_scatter_cols<<<rw_blocks(N * Lc, 256), 256, 0, st>>>(Uc, Lc, N, prob, K, k0);
-    RW_LAUNCH_CHECK();
+    if (nchunks > 1) {
+      k_scatter_cols<<<rw_blocks(N * Lc, 256), 256, 0, st>>>(Uc, Lc, N, prob, K, k0);
+      RW_LAUNCH_CHECK();
+    }
   }
   return RW_OK;
 }
