@@ -22,17 +22,17 @@ namespace {
 __device__ __forceinline__ int clampi(int v, int n) { return v < 0 ? 0 : (v >= n ? n - 1 : v); }
 
 // B[((ze * EY + ye) * DX + x) * K + k] = sum over t in [0, 2h] of A_k at extended (x + t, ye, ze),
-// i.e. of |F - M(. + d_k)| at image coordinates (x + t - h, ye - h, ze - h), clamped
+// i.e. of |F - M(. + d_k)| at image coordinates (x + t - h, ye - h, ze - h), clamped.
+// Grid: (row of DX K entries in blocks, ye, ze).
 __global__ void __launch_bounds__(256)
 k_reg_absdiff_x(const float* __restrict__ F, const float* __restrict__ M, int ndim, int DX,
                 int DY, int DZ, const int32_t* __restrict__ disp, int K, int h, int EY, int EZ,
                 float* __restrict__ B) {
-  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t total = (int64_t)DX * EY * EZ * K;
-  if (e >= total) return;
-  const int64_t v = e / K;
-  const int k = (int)(e - v * K);
-  const int x0 = (int)(v % DX), ye = (int)((v / DX) % EY), ze = (int)(v / ((int64_t)DX * EY));
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;   // entry of the row: x K + k
+  if (r >= DX * K) return;
+  const int x0 = r / K, k = r - x0 * K;
+  const int ye = blockIdx.y, ze = blockIdx.z;
+  const int64_t e = ((int64_t)ze * EY + ye) * DX * K + r;
   const int y = ye - (EY > DY ? h : 0), z = ze - (EZ > DZ ? h : 0);
   const int dx = disp[k * ndim + 0], dy = disp[k * ndim + 1];
   const int dz = ndim == 3 ? disp[k * ndim + 2] : 0;
@@ -47,21 +47,19 @@ k_reg_absdiff_x(const float* __restrict__ F, const float* __restrict__ M, int nd
 }
 
 // out[(z, y, x) in the output box][k] = sum over t in [0, 2h] of in[(z, y, x) + t along axis][k],
-// in has extent (IX, IY, IZ), out (OX, OY, OZ) with the summed axis shorter by 2 h
+// in has extent (IX, IY, IZ), out (OX, OY, OZ) with the summed axis shorter by 2 h.
+// Grid: (row of OX K entries in blocks, y, z).
 __global__ void __launch_bounds__(256)
 k_reg_box(const float* __restrict__ in, int IX, int IY, int axis, int h, int OX, int OY, int OZ,
           int K, float* __restrict__ out) {
-  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t total = (int64_t)OX * OY * OZ * K;
-  if (e >= total) return;
-  const int64_t v = e / K;
-  const int k = (int)(e - v * K);
-  const int x = (int)(v % OX), y = (int)((v / OX) % OY), z = (int)(v / ((int64_t)OX * OY));
-  const int64_t step = axis == 0 ? 1 : (axis == 1 ? (int64_t)IX : (int64_t)IX * IY);
-  const int64_t base = (((int64_t)z * IY + y) * IX + x) * K + k;
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;   // x K + k
+  if (r >= OX * K) return;
+  const int y = blockIdx.y, z = blockIdx.z;
+  const int64_t step = (axis == 0 ? 1 : (axis == 1 ? (int64_t)IX : (int64_t)IX * IY)) * K;
+  const int64_t base = ((int64_t)z * IY + y) * IX * K + r;
   float s = 0.f;
-  for (int t = 0; t <= 2 * h; ++t) s += __ldg(in + base + t * step * K);
-  out[e] = s;
+  for (int t = 0; t <= 2 * h; ++t) s += __ldg(in + base + t * step);
+  out[((int64_t)z * OY + y) * OX * K + r] = s;
 }
 
 // the box sum along `axis` (as k_reg_box, output extent (OX, OY, OZ) = the image) and the
@@ -69,20 +67,19 @@ k_reg_box(const float* __restrict__ in, int IX, int IY, int axis, int h, int OX,
 // lo = min_k s_k^2; the block's sums and priors are contiguous, read and written coalesced
 constexpr int kNormVox = 32;
 
+// Grid: (32-voxel segments of a row, y, z).
 __global__ void __launch_bounds__(256)
 k_reg_box_norm(const float* __restrict__ in, int IX, int IY, int axis, int h, int OX, int OY,
-               int64_t N, int K, float* __restrict__ P) {
+               int K, float* __restrict__ P) {
   extern __shared__ float sbuf[];   // kNormVox x K sums
-  const int64_t v0 = (int64_t)blockIdx.x * kNormVox;
-  const int nv = (int)(N - v0 < kNormVox ? N - v0 : kNormVox);
+  const int x0 = blockIdx.x * kNormVox, y = blockIdx.y, z = blockIdx.z;
+  const int nv = OX - x0 < kNormVox ? OX - x0 : kNormVox;
   const int64_t step = (axis == 0 ? 1 : (axis == 1 ? (int64_t)IX : (int64_t)IX * IY)) * K;
+  const int64_t base = (((int64_t)z * IY + y) * IX + x0) * K;
+  const int64_t v0 = ((int64_t)z * OY + y) * OX + x0;
   for (int e = threadIdx.x; e < nv * K; e += blockDim.x) {
-    const int64_t v = v0 + e / K;
-    const int k = e % K;
-    const int x = (int)(v % OX), y = (int)((v / OX) % OY), z = (int)(v / ((int64_t)OX * OY));
-    const int64_t base = (((int64_t)z * IY + y) * IX + x) * K + k;
     float s = 0.f;
-    for (int t = 0; t <= 2 * h; ++t) s += __ldg(in + base + t * step);
+    for (int t = 0; t <= 2 * h; ++t) s += __ldg(in + base + e + t * step);
     sbuf[e] = s;
   }
   __syncthreads();
@@ -128,19 +125,21 @@ extern "C" rw_status rw_registration_priors(const float* fixed_dev, const float*
   float* C = B + nb;
   // x (fused with the differences): -> (DX, EY, EZ); 3-D y: -> (DX, DY, EZ); last axis with the
   // normalization: -> (DX, DY, DZ)
-  k_reg_absdiff_x<<<rw_blocks(nb, 256), 256, 0, st>>>(fixed_dev, moving_dev, ndim, DX, DY, DZ,
-                                                      disp_dev, K, half, EY, EZ, B);
+  if (DX * K > (1 << 30) || EY > 65535 || EZ > 65535) return RW_ERR_UNSUPPORTED;
+  const unsigned rowblk = (unsigned)((DX * K + 255) / 256);
+  k_reg_absdiff_x<<<dim3(rowblk, EY, EZ), 256, 0, st>>>(fixed_dev, moving_dev, ndim, DX, DY, DZ,
+                                                        disp_dev, K, half, EY, EZ, B);
   RW_LAUNCH_CHECK();
   if (norm_shm > 48 * 1024)
     RW_CHECK_CUDA(cudaFuncSetAttribute(k_reg_box_norm, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)norm_shm));
-  const unsigned nblk = (unsigned)((N + kNormVox - 1) / kNormVox);
+  const dim3 ngrid((unsigned)((DX + kNormVox - 1) / kNormVox), DY, DZ);
   if (ndim == 3) {
-    k_reg_box<<<rw_blocks(nc, 256), 256, 0, st>>>(B, DX, EY, 1, half, DX, DY, EZ, K, C);
+    k_reg_box<<<dim3(rowblk, DY, EZ), 256, 0, st>>>(B, DX, EY, 1, half, DX, DY, EZ, K, C);
     RW_LAUNCH_CHECK();
-    k_reg_box_norm<<<nblk, 256, norm_shm, st>>>(C, DX, DY, 2, half, DX, DY, N, K, priors_dev);
+    k_reg_box_norm<<<ngrid, 256, norm_shm, st>>>(C, DX, DY, 2, half, DX, DY, K, priors_dev);
   } else {
-    k_reg_box_norm<<<nblk, 256, norm_shm, st>>>(B, DX, EY, 1, half, DX, DY, N, K, priors_dev);
+    k_reg_box_norm<<<ngrid, 256, norm_shm, st>>>(B, DX, EY, 1, half, DX, DY, K, priors_dev);
   }
   RW_LAUNCH_CHECK();
   RW_CHECK_CUDA(cudaFreeAsync(scratch, st));
