@@ -1338,6 +1338,8 @@ __device__ void adapt_body(const float* __restrict__ G, int ldg, const float* __
     // constrained solution's mu grows with m, so the warm start stays on the left of the root,
     // where the iteration is monotone).
     __shared__ float s_muw[RW_MAX_LABELS];
+    __shared__ int cand_fail;
+    const float fail_thr = 1.05f * (float)fmax;
     if (tid < RW_MAX_LABELS) s_muw[tid] = 0.f;
     __syncthreads();
     (void)rows_done;
@@ -1360,7 +1362,22 @@ __device__ void adapt_body(const float* __restrict__ G, int ldg, const float* __
         s2 = warp_sum(s2);
         if (lane == 0) nk[k] = sqrtf(s2);
       }
+      // Lower bounds of f_k by Lagrangian duality: for a shift mu >= 0 and a = (G + mu I)^{-1} b,
+      // f_k >= ||u_k||^2 - a^T b - mu rho^2.  One label whose bound exceeds f_max (with a 5%
+      // margin for the FP32 arithmetic) fails the candidate whatever the others give, so the
+      // Newton iterations of a failing candidate stop there; a passing candidate is solved
+      // exactly as before.
+      if (tid == 0) cand_fail = 0;
       __syncthreads();
+      for (int k = warp; k < L; k += nw) {
+        if (!(nk[k] > (float)rho)) continue;
+        float t = 0.f;
+        for (int i = lane; i < m; i += 32) t = fmaf(al[k * mmax + i], bv[(int64_t)i * ldb + k], t);
+        t = warp_sum(t);
+        if (lane == 0 && ck[k] - t - mu0 * (float)(rho * rho) > fail_thr) cand_fail = 1;
+      }
+      __syncthreads();
+      if (cand_fail) continue;   // (uniform) the next candidate
       bool refactored = false;   // B2 still holds the factor of G_m + mu0 I
       for (int k = 0; k < L && okc; ++k) {
         if (!(nk[k] > (float)rho)) continue;
@@ -1402,20 +1419,35 @@ __device__ void adapt_body(const float* __restrict__ G, int ldg, const float* __
           __syncthreads();
           if (!chol_lower_smem(B2, m, mss)) { okc = false; break; }
           if (warp == 0) {
-            for (int i = lane; i < m; i += 32) z[k * mmax + i] = bv[(int64_t)i * ldb + k];
+            float t = 0.f;
+            for (int i = lane; i < m; i += 32) {
+              const float bi = bv[(int64_t)i * ldb + k];
+              z[k * mmax + i] = bi;
+            }
             __syncwarp();
             fwd_lower_warp(B2, m, mss, z + k * mmax, z + k * mmax);
             bwd_lowerT_warp(B2, m, mss, z + k * mmax, al + k * mmax);
             float s2 = 0.f;
-            for (int i = lane; i < m; i += 32) s2 = fmaf(al[k * mmax + i], al[k * mmax + i], s2);
+            for (int i = lane; i < m; i += 32) {
+              s2 = fmaf(al[k * mmax + i], al[k * mmax + i], s2);
+              t = fmaf(al[k * mmax + i], bv[(int64_t)i * ldb + k], t);
+            }
             s2 = warp_sum(s2);
-            if (lane == 0) nk[k] = sqrtf(s2);
+            t = warp_sum(t);
+            if (lane == 0) {
+              nk[k] = sqrtf(s2);
+              if (ck[k] - t - mu * (float)(rho * rho) > fail_thr) cand_fail = 1;   // dual bound
+            }
           }
+          __syncthreads();
+          if (cand_fail) break;
         }
         __syncthreads();
         if (tid == 0) s_muw[k] = mu;   // the next candidate's start for this label
+        if (cand_fail) break;
       }
       __syncthreads();
+      if (cand_fail) continue;
       seed_residuals(Qs, ldq, Us, ldu, S, L, m, al, fk, mmax);
       bool pass = okc;
       for (int k = 0; k < L; ++k)
