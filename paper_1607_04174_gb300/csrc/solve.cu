@@ -1395,11 +1395,20 @@ __device__ void adapt_body(const float* __restrict__ G, int ldg, const float* __
             __syncwarp();
             fwd_lower_warp(B2, m, mss, z + k * mmax, z + k * mmax);
             bwd_lowerT_warp(B2, m, mss, z + k * mmax, al + k * mmax);
-            float s2 = 0.f;
-            for (int i = lane; i < m; i += 32) s2 = fmaf(al[k * mmax + i], al[k * mmax + i], s2);
+            float s2 = 0.f, t = 0.f;
+            for (int i = lane; i < m; i += 32) {
+              s2 = fmaf(al[k * mmax + i], al[k * mmax + i], s2);
+              t = fmaf(al[k * mmax + i], bv[(int64_t)i * ldb + k], t);
+            }
             s2 = warp_sum(s2);
-            if (lane == 0) nk[k] = sqrtf(s2);
+            t = warp_sum(t);
+            if (lane == 0) {
+              nk[k] = sqrtf(s2);
+              if (ck[k] - t - mu * (float)(rho * rho) > fail_thr) cand_fail = 1;   // dual bound
+            }
           }
+          __syncthreads();
+          if (cand_fail) break;
         }
         refactored = true;
         for (int it = 0; it < 12; ++it) {
