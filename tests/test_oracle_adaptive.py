@@ -101,3 +101,27 @@ def test_g_residual_and_sampling():
     lab = adaptive.sampled_labels((31, 31, 13), r=4)
     assert lab.size == 8 * 8 * 4
     assert adaptive.sampled_labels((3, 3, 3), r=4).tolist() == [13]   # the centre label
+
+
+def test_dual_bound_is_below_the_constrained_minimum():
+    """The GPU's adaptive choice rejects a candidate m as soon as one label's Lagrangian dual
+    bound g(mu) = ||u||^2 - b^T (G + mu I)^{-1} b - mu rho^2 (G = A^T A, b = A^T u) exceeds
+    f_max.  Weak duality makes g(mu) a lower bound of the constrained minimum f for every
+    mu >= 0, reaching it at the optimal multiplier; checked here against the oracle's
+    trust-region solve on underdetermined fits (more columns than rows, the active case)."""
+    rng = np.random.default_rng(17)
+    for trial in range(20):
+        S, m = int(rng.integers(4, 12)), int(rng.integers(12, 30))
+        A = rng.standard_normal((S, m))
+        u = rng.standard_normal(S)
+        G, b = A.T @ A, A.T @ u
+        _, alpha_ls, _ = adaptive.trust_region_ls(A, u, 1e30)
+        rho = 0.3 * np.linalg.norm(alpha_ls)          # the constraint is active
+        f, alpha, mu_star = adaptive.trust_region_ls(A, u, rho)
+        assert mu_star > 0
+        for mu in np.concatenate([np.geomspace(1e-6, 1e3, 25), [mu_star]]):
+            a = np.linalg.solve(G + mu * np.eye(m), b)
+            g = u @ u - a @ b - mu * rho ** 2
+            assert g <= f + 1e-9 * max(1.0, f), (trial, mu, g, f)
+        a = np.linalg.solve(G + mu_star * np.eye(m), b)
+        assert abs((u @ u - a @ b - mu_star * rho ** 2) - f) <= 1e-7 * max(1.0, f)
