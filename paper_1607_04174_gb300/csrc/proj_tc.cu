@@ -307,15 +307,6 @@ k_backproject_tc(const T* __restrict__ Qp, int64_t N, int nchunk_max,
 constexpr int kProjThreads = 320;
 constexpr int kLabAhead = 4, kLabRing = 8;
 
-template <int N>
-__device__ __forceinline__ void cp_async_wait_le(int pending) {   // wait_group(min(pending, N))
-  if (pending >= N) cp_async_wait<N>();
-  else if (pending == 3) cp_async_wait<3>();
-  else if (pending == 2) cp_async_wait<2>();
-  else if (pending == 1) cp_async_wait<1>();
-  else cp_async_wait<0>();
-}
-
 template <typename T, int NL>
 __global__ void __launch_bounds__(kProjThreads, 1)
 k_project_tc(const T* __restrict__ Qp, int64_t N, int nchunk_max,
@@ -406,7 +397,7 @@ k_project_tc(const T* __restrict__ Qp, int64_t N, int nchunk_max,
       fetch_label(j + kLabAhead);
       cp_async_commit();
       if (!mbar_wait_limited(&full[st], (unsigned)(j / nst) & 1u, status, abort)) break;
-      cp_async_wait_le<kLabAhead>(kLabAhead);   // this tile's label (kLabAhead groups after it)
+      cp_async_wait<kLabAhead>();   // this tile's label (kLabAhead groups after it)
       char* stg = sm + st * SB;
       const bool in = pt < rows_of(j);
       const int lab = labring[j % kLabRing][pt];

@@ -9,7 +9,8 @@
 // definition's), computed as one pass per axis of 2 h + 1 taps.  Every buffer is voxel-major
 // with the K labels interleaved (label fastest), so each pass reads and writes coalesced:
 //   k_reg_absdiff_x: A summed along x, computed from F and M on the fly (the extended grid
-//                    shrunk back to the image along x);
+//                    shrunk back to the image along x; k_reg_absdiff_x_win for K <= 32 labels
+//                    forms each difference once, in a sliding register window);
 //   k_reg_box:       the sum along the middle axis (3-D: y);
 //   k_reg_box_norm:  the sum along the last axis and the normalization, 32 voxels per block:
 //                    the sums go through shared memory and one thread per voxel takes the
@@ -60,6 +61,42 @@ k_reg_box(const float* __restrict__ in, int IX, int IY, int axis, int h, int OX,
   float s = 0.f;
   for (int t = 0; t <= 2 * h; ++t) s += __ldg(in + base + t * step);
   out[((int64_t)z * OY + y) * OX * K + r] = s;
+}
+
+// The same x pass for K <= 32 labels and half-width H: a warp takes 32 consecutive x of one
+// row, lane = label; each difference is formed once and kept in a register window of 2 H + 1
+// values, summed in the same order as above (same results).  Grid: (x segments of 128, ye, ze).
+template <int H>
+__global__ void __launch_bounds__(128)
+k_reg_absdiff_x_win(const float* __restrict__ F, const float* __restrict__ M, int ndim, int DX,
+                    int DY, int DZ, const int32_t* __restrict__ disp, int K, int EY, int EZ,
+                    float* __restrict__ B) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int x0 = (blockIdx.x * 4 + warp) * 32;
+  if (x0 >= DX) return;
+  const int ye = blockIdx.y, ze = blockIdx.z;
+  const int y = ye - (EY > DY ? H : 0), z = ze - (EZ > DZ ? H : 0);
+  const bool act = lane < K;
+  const int k = act ? lane : 0;
+  const int dx = disp[k * ndim + 0], dy = disp[k * ndim + 1];
+  const int dz = ndim == 3 ? disp[k * ndim + 2] : 0;
+  const float* Fr = F + ((int64_t)clampi(z, DZ) * DY + clampi(y, DY)) * DX;
+  const float* Mr = M + ((int64_t)clampi(z + dz, DZ) * DY + clampi(y + dy, DY)) * DX;
+  auto diff = [&](int x) { return fabsf(__ldg(Fr + clampi(x, DX)) - __ldg(Mr + clampi(x + dx, DX))); };
+  float win[2 * H + 1];
+#pragma unroll
+  for (int t = 0; t < 2 * H; ++t) win[t] = diff(x0 - H + t);
+  const int x1 = min(DX, x0 + 32);
+  float* out = B + ((int64_t)ze * EY + ye) * DX * K + k;
+  for (int x = x0; x < x1; ++x) {
+    win[2 * H] = diff(x + H);
+    float sum = win[0];
+#pragma unroll
+    for (int t = 1; t <= 2 * H; ++t) sum += win[t];
+    if (act) out[(int64_t)x * K] = sum;
+#pragma unroll
+    for (int t = 0; t < 2 * H; ++t) win[t] = win[t + 1];
+  }
 }
 
 // the box sum along `axis` (as k_reg_box, output extent (OX, OY, OZ) = the image) and the
@@ -127,8 +164,19 @@ extern "C" rw_status rw_registration_priors(const float* fixed_dev, const float*
   // normalization: -> (DX, DY, DZ)
   if (DX * K > (1 << 30) || EY > 65535 || EZ > 65535) return RW_ERR_UNSUPPORTED;
   const unsigned rowblk = (unsigned)((DX * K + 255) / 256);
-  k_reg_absdiff_x<<<dim3(rowblk, EY, EZ), 256, 0, st>>>(fixed_dev, moving_dev, ndim, DX, DY, DZ,
-                                                        disp_dev, K, half, EY, EZ, B);
+  const dim3 wgrid((unsigned)((DX + 127) / 128), EY, EZ);
+  if (K <= 32 && half == 1)
+    k_reg_absdiff_x_win<1><<<wgrid, 128, 0, st>>>(fixed_dev, moving_dev, ndim, DX, DY, DZ,
+                                                 disp_dev, K, EY, EZ, B);
+  else if (K <= 32 && half == 2)
+    k_reg_absdiff_x_win<2><<<wgrid, 128, 0, st>>>(fixed_dev, moving_dev, ndim, DX, DY, DZ,
+                                                 disp_dev, K, EY, EZ, B);
+  else if (K <= 32 && half == 3)
+    k_reg_absdiff_x_win<3><<<wgrid, 128, 0, st>>>(fixed_dev, moving_dev, ndim, DX, DY, DZ,
+                                                 disp_dev, K, EY, EZ, B);
+  else
+    k_reg_absdiff_x<<<dim3(rowblk, EY, EZ), 256, 0, st>>>(fixed_dev, moving_dev, ndim, DX, DY,
+                                                          DZ, disp_dev, K, half, EY, EZ, B);
   RW_LAUNCH_CHECK();
   if (norm_shm > 48 * 1024)
     RW_CHECK_CUDA(cudaFuncSetAttribute(k_reg_box_norm, cudaFuncAttributeMaxDynamicSharedMemorySize,
