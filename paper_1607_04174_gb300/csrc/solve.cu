@@ -328,9 +328,11 @@ __global__ void k_seed_gather(const int32_t* __restrict__ idx, const int32_t* __
                               int DX, int DY, int DZ, const int32_t* __restrict__ rowptr,
                               const int32_t* __restrict__ colv, const float* __restrict__ ccsr,
                               float gamma, float* __restrict__ Bcat, int ldb,
-                              float* __restrict__ gnull, float ginv) {
+                              float* __restrict__ gnull, float ginv,
+                              int* __restrict__ mflag) {
   rw_grid_wait();
   rw_grid_trigger();
+  if (mflag && blockIdx.x == 0 && threadIdx.x == 0) *mflag = 0;   // m not yet published
   const int lane = threadIdx.x & 31;
   const int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (t >= S) return;
@@ -1617,9 +1619,18 @@ k_project(const T* __restrict__ Q, int ldq, int cpr, const float* __restrict__ p
 __global__ void k_reduce_partials(const float* __restrict__ part, int nblk, int ldq, int lp,
                                   int mq, float scale, float* __restrict__ Z,
                                   const double* __restrict__ lam, double gamma, int m,
-                                  float* __restrict__ lgam) {
-  rw_grid_trigger();  // the small solve's prologue only reads results older than the projection
-  rw_grid_wait();
+                                  float* __restrict__ lgam, int wait_first) {
+  // The small solve's prologue reads the factors of k_adapt_lu.  Behind an ordinary
+  // projection they are complete once the projection has started, so the trigger comes first;
+  // behind an early one (started before k_adapt_lu ends, waiting for it before it exits) they
+  // are complete only once the projection has ended, so the wait comes first.
+  if (wait_first) {
+    rw_grid_wait();
+    rw_grid_trigger();
+  } else {
+    rw_grid_trigger();
+    rw_grid_wait();
+  }
   // one warp per entry of Z: lane l adds the partials l, l + 32, ... in order, then a fixed
   // butterfly; also lgam = lambda + gamma in FP32 for the small system
   const int lane = threadIdx.x & 31;
@@ -2038,6 +2049,10 @@ k_adapt_lu(const float* __restrict__ G, int ldg, const float* __restrict__ bv, i
       *reinterpret_cast<volatile int*>(rh) = mmax;
       *reinterpret_cast<volatile int*>(rf) = mmax;
     }
+    // m is final (thread 0 wrote mdev[0] above): publish it for a projection that starts
+    // before this kernel ends (k_project_tma with early = 1); the factors are not covered
+    if (threadIdx.x == 0)
+      asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(mdev + 3), "r"(1) : "memory");
     cl.sync();
   } else {
     lu_body(cl, mmax, Kg, ldk, lam, gamma, F, ldf, luinv, mdev, &s_hint, &s_final);
@@ -2045,8 +2060,9 @@ k_adapt_lu(const float* __restrict__ G, int ldg, const float* __restrict__ bv, i
 }
 
 // C = M^{-1} (h + gamma Z) from the factors of k_adapt_lu.  Before the grid dependency wait
-// (the factors come from two launches back, complete once the projection has started) the
-// factors are copied in; after it the substitutions run by 32-row blocks: one warp solves the
+// (the factors come from two launches back and are complete when this kernel starts: behind an
+// ordinary projection, which started after k_adapt_lu ended; behind an early one,
+// k_reduce_partials lets this kernel start only after its own wait) the factors are copied in; after it the substitutions run by 32-row blocks: one warp solves the
 // diagonal block for all labels (lane = row, labels in registers), then all threads update the
 // remaining rows.  When the factorization was flagged unstable the whole pivoting solve runs
 // instead.
@@ -2364,13 +2380,37 @@ k_project_cw(const T* __restrict__ Qp, int64_t N, int nchunk_max, const float* _
 // sums them over the warp and the warp adds them to its own accumulator (step order: fixed);
 // the warps are added in order at the end.  Block partials as k_project_cw writes them.
 constexpr int kPtRows = 1024, kPtStages = 4, kPtRowsPerThread = kPtRows / 256;
+constexpr int kEarlyPolls = 1 << 16;   // x (up to 2 us + an L2 round trip): about 0.15 s
 
 template <typename T, int LP>
 __global__ void __launch_bounds__(256, 2)
 k_project_tma(const T* __restrict__ Qp, int64_t N, int nchunk_max, const float* __restrict__ phat,
               const int* __restrict__ seedlab, const int* __restrict__ mdev,
-              int64_t rows_per_block, float* __restrict__ part, int* status) {
-  rw_grid_wait();
+              int64_t rows_per_block, float* __restrict__ part, int* status, int early) {
+  // early: the preceding kernel is k_adapt_lu, whose LU half may still run after m is final.
+  // Its other inputs (basis, priors, seed labels) are complete once it has started, so the
+  // block starts as soon as mdev[3] says m is published (a bounded poll; on time-out, the
+  // ordinary grid wait) and waits for the whole predecessor only before it exits, so that
+  // the kernels after it still see every output of k_adapt_lu.
+  __shared__ int s_m;
+  if (early) {
+    if (threadIdx.x == 0) {
+      int v = 0, mm = -1;
+      unsigned ns = 128;   // back-off doubling to 2 us: few L2 requests while a long choice runs
+      for (int it = 0; it < kEarlyPolls; ++it) {
+        asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(mdev + 3) : "memory");
+        if (v) break;
+        __nanosleep(ns);
+        ns = ns < 2048u ? 2u * ns : 2048u;
+      }
+      if (v) asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(mm) : "l"(mdev) : "memory");
+      s_m = mm;
+    }
+    __syncthreads();
+    if (s_m < 0) rw_grid_wait();
+  } else {
+    rw_grid_wait();
+  }
   rw_grid_trigger();
   constexpr int NV = 8 * LP, NG = NV / 32;
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -2378,7 +2418,7 @@ k_project_tma(const T* __restrict__ Qp, int64_t N, int nchunk_max, const float* 
   float* red = reinterpret_cast<float*>(stage + kPtStages * kPtRows);  // nw x nchunk_max x NV
   __shared__ __align__(8) uint64_t bar[kPtStages];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
-  const int m = mdev[0];
+  const int m = (early && s_m >= 0) ? s_m : mdev[0];
   const int nch = min((m + 7) / 8, nchunk_max);
   const int64_t r0 = (int64_t)blockIdx.x * rows_per_block;
   const int64_t r1 = min(N, r0 + rows_per_block);
@@ -2457,6 +2497,7 @@ k_project_tma(const T* __restrict__ Qp, int64_t N, int nchunk_max, const float* 
       for (int w = 0; w < nw; ++w) v += red[(size_t)w * nchunk_max * NV + e];
     pb[e] = v;
   }
+  if (early) rw_grid_wait();
 }
 
 constexpr int kBackChunks = 8;  // 16-byte chunks per row in flight in the back-projection
@@ -2862,7 +2903,8 @@ template <typename T, int LP>
 rw_status launch_proj_back(bool back, const T* Q, int ldq, const float* phat,
                            const int* seedlab, const rw_graph* g, const int* mdev, float* part,
                            int nblk, const float* C, float cscale, float* xhat, float* U,
-                           uint8_t* labels, int L, int* clear, const float* nul, cudaStream_t st) {
+                           uint8_t* labels, int L, int* clear, const float* nul, cudaStream_t st,
+                           int early = 0) {
   constexpr int V = Vec16<T>::V;
   const int cpr = ldq / V;
   if constexpr (V == 8) {  // 16-bit copies: panel-major layout, ldq = 8 x chunks
@@ -2879,7 +2921,7 @@ rw_status launch_proj_back(bool back, const T* Q, int ldq, const float* phat,
         const size_t shm = sizeof(uint4) * kPtStages * kPtRows + sizeof(float) * 8 * (size_t)nchunk * 8 * LP;
         RW_CHECK_CUDA(ensure_smem(k_project_tma<T, LP>, shm));
         RW_LAUNCH((k_project_tma<T, LP>), nblk, 256, shm, st, Q, g->N, nchunk, phat, seedlab, mdev,
-                  rpb, part, g->status);
+                  rpb, part, g->status, early);
       } else {
         const size_t shm = sizeof(float) * kParts * (size_t)nchunk * 8 * LP;
         if (shm > 48 * 1024)
@@ -2922,10 +2964,10 @@ template <typename T>
 rw_status proj_back(int lp, bool back, const T* Q, int ldq, const float* phat, const int* seedlab,
                     const rw_graph* g, const int* mdev, float* part, int nblk, const float* C,
                     float cscale, float* xhat, float* U, uint8_t* labels, int L, cudaStream_t st, int* clear = nullptr,
-                    const float* nul = nullptr) {
+                    const float* nul = nullptr, int early = 0) {
   switch (lp) {
-    case 4: return launch_proj_back<T, 4>(back, Q, ldq, phat, seedlab, g, mdev, part, nblk, C, cscale, xhat, U, labels, L, clear, nul, st);
-    case 8: return launch_proj_back<T, 8>(back, Q, ldq, phat, seedlab, g, mdev, part, nblk, C, cscale, xhat, U, labels, L, clear, nul, st);
+    case 4: return launch_proj_back<T, 4>(back, Q, ldq, phat, seedlab, g, mdev, part, nblk, C, cscale, xhat, U, labels, L, clear, nul, st, early);
+    case 8: return launch_proj_back<T, 8>(back, Q, ldq, phat, seedlab, g, mdev, part, nblk, C, cscale, xhat, U, labels, L, clear, nul, st, early);
     case 16: return launch_proj_back<T, 16>(back, Q, ldq, phat, seedlab, g, mdev, part, nblk, C, cscale, xhat, U, labels, L, clear, nul, st);
     default:   // 32 labels per pass: the tensor-core kernels only
       if constexpr (Vec16<T>::V == 8) {
@@ -3379,7 +3421,7 @@ extern "C" rw_status rw_solve(const rw_graph* g, const rw_basis* b, const int32_
   RW_LAUNCH(k_seed_gather, rw_blocks((int64_t)S * 32, 256), 256, 0, st, 
       seed_idx_dev, seed_lab_dev, S, L, lp, g->N, b->Q32, b->ld32, mp, seedlab, g->cw, g->d,
       g->sq, g->normalized, g->kind, g->ndim, g->dims[0], g->dims[1], g->dims[2], g->rowptr,
-      g->col, g->ccsr, (float)gamma, Bcat, wcat, gnull, ginv);
+      g->col, g->ccsr, (float)gamma, Bcat, wcat, gnull, ginv, mdev + 3);
   float* part = reinterpret_cast<float*>(P(lay.part));
   float* Z = reinterpret_cast<float*>(P(lay.Z));
   float* lgam = Z + (size_t)mq * lp;
@@ -3402,15 +3444,22 @@ extern "C" rw_status rw_solve(const rw_graph* g, const rw_basis* b, const int32_
   const int nblk_p = fmt == RW_BASIS_F32 ? nblk : (tc_p ? sms : proj_per_sm * sms);
   float zscale = (fmt == RW_BASIS_F16 ? 1.f / b->qscale : 1.f) / (tc_p ? kTcProjScale : 1.f);
   float cscale = fmt == RW_BASIS_F16 ? 1.f / b->qscale : 1.f;
-  auto project = [&]() -> rw_status {
+  // early (behind the fused k_adapt_lu at a fixed m, on the bulk-copy kernel only): m is
+  // published as the kernel starts, so the projection runs beside the whole LU of the m x m
+  // system; two SMs hold that cluster, so the grid leaves them out and every block is
+  // resident at once.  (With m chosen adaptively the choice ends only a few microseconds
+  // before the LU, and the overlap measured no faster.)
+  auto project = [&](bool early) -> rw_status {
+    const int nb = early ? proj_per_sm * (sms - 2) : nblk_p;
+    const int ef = early ? 1 : 0;
     if (fmt == RW_BASIS_F16)
-      RW_TRY(proj_back<__half>(lp, false, b->Q16, ldq_e, phat, seedlab, g, mdev, part, nblk_p, nullptr, 0.f, nullptr, nullptr, nullptr, L, st));
+      RW_TRY(proj_back<__half>(lp, false, b->Q16, ldq_e, phat, seedlab, g, mdev, part, nb, nullptr, 0.f, nullptr, nullptr, nullptr, L, st, nullptr, nullptr, ef));
     else if (fmt == RW_BASIS_BF16)
-      RW_TRY(proj_back<__nv_bfloat16>(lp, false, b->Qbf, ldq_e, phat, seedlab, g, mdev, part, nblk_p, nullptr, 0.f, nullptr, nullptr, nullptr, L, st));
+      RW_TRY(proj_back<__nv_bfloat16>(lp, false, b->Qbf, ldq_e, phat, seedlab, g, mdev, part, nb, nullptr, 0.f, nullptr, nullptr, nullptr, L, st, nullptr, nullptr, ef));
     else
-      RW_TRY(proj_back<float>(lp, false, b->Q32, ldq_e, phat, seedlab, g, mdev, part, nblk_p, nullptr, 0.f, nullptr, nullptr, nullptr, L, st));
+      RW_TRY(proj_back<float>(lp, false, b->Q32, ldq_e, phat, seedlab, g, mdev, part, nb, nullptr, 0.f, nullptr, nullptr, nullptr, L, st));
     RW_LAUNCH(k_reduce_partials, rw_blocks((int64_t)std::max(mq * lp, m_max) * 32, 256), 256, 0, st, 
-        part, nblk_p, ldq_e, lp, mq, zscale, Z, b->lam, gamma, m_max, lgam);
+        part, nb, ldq_e, lp, mq, zscale, Z, b->lam, gamma, m_max, lgam, ef);
     return RW_OK;
   };
   if (g0) {
@@ -3421,7 +3470,7 @@ extern "C" rw_status rw_solve(const rw_graph* g, const rw_basis* b, const int32_
     else if (lp == 8) RW_LAUNCH(k_null_fill<8>, fblk, 256, 0, st, phat, g->sq, g->N, ginv);
     else RW_LAUNCH(k_null_fill<16>, fblk, 256, 0, st, phat, g->sq, g->N, ginv);
     RW_LAUNCH(k_set_m, 1, 32, 0, st, mdev, m_max);
-    RW_TRY(project());
+    RW_TRY(project(false));
     float* partw = reinterpret_cast<float*>(P(lay.partw));
     const int ny = std::max(1, std::min(kNullSplit, (S + 255) / 256));
     RW_LAUNCH(k_null_w, dim3((m_max + 31) / 32, ny), 256, 0, st, Qs, wcat, gnull, S, m_max,
@@ -3478,7 +3527,7 @@ extern "C" rw_status rw_solve(const rw_graph* g, const rw_basis* b, const int32_
   }
   RW_TRY(mark(3));
   // Z = Q_n^T P-hat_n (gamma = 0: no priors; Z was zeroed by k_null_row0)
-  if (!g0) RW_TRY(project());
+  if (!g0) RW_TRY(project(fused && !adaptive && fmt != RW_BASIS_F32 && !tc_p && lp <= 8 && sms > 8));
   else if (fused) RW_LAUNCH(k_pdl_fence, 1, 32, 0, st, 0);
   RW_TRY(mark(4));
   // small system
@@ -3841,7 +3890,7 @@ static rw_status unseeded_passes(const rw_graph* g, const rw_basis* b, const T* 
     RW_TRY(proj_back<T>(lp, false, Q, ldq, phat, seedlab, g, mall, part, nblk_p, nullptr, 0.f,
                         nullptr, nullptr, nullptr, Lc, st));
     RW_LAUNCH(k_reduce_partials, rw_blocks((int64_t)std::max(mq * lp, m_max) * 32, 256), 256, 0,
-              st, part, nblk_p, ldq, lp, mq, zscale, Z, b->lam, gamma, m_max, lgam);
+              st, part, nblk_p, ldq, lp, mq, zscale, Z, b->lam, gamma, m_max, lgam, 0);
     k_store_z<<<rw_blocks((int64_t)m_max * Lc, 256), 256, 0, st>>>(Z, lp, Lc, k0, m_max, K, Zall);
     RW_LAUNCH_CHECK();
   }

@@ -42,6 +42,22 @@ def test_mbarrier_waits_are_bounded():
     assert re.search(r"it\s*>\s*\(1\s*<<\s*\d+\)", body)
 
 
+def test_flag_polls_are_bounded():
+    """The one poll on a flag in global memory (the projection that starts once the adaptive
+    choice has published m) runs at most kEarlyPolls times and then takes the ordinary grid
+    dependency wait, which ends when its predecessor ends."""
+    src = {f: _strip_comments(t) for f, t in _sources().items()}
+    polls = [f for f, t in src.items() for _ in re.finditer(r"ld\.acquire", t)]
+    assert polls == ["solve.cu"]
+    t = src["solve.cu"]
+    assert re.search(r"constexpr int kEarlyPolls = 1 << 16;", t)
+    i = t.index("ld.acquire")
+    loop = t[t.rindex("for (", 0, i):i]
+    assert re.match(r"for \(int it = 0; it < kEarlyPolls; \+\+it\)", loop)
+    tail = t[i:t.index("__syncthreads();", i) + 200]
+    assert "if (s_m < 0) rw_grid_wait();" in tail
+
+
 def test_no_device_traps_or_asserts():
     for f, t in _sources().items():
         t = _strip_comments(t)
