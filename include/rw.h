@@ -393,8 +393,8 @@ rw_status rw_grad_fast(const rw_graph* g, const rw_basis* b, const int32_t* seed
  * (RW_ERR_INVALID_ARG otherwise).
  * Scratch: a fixed device array inside the library (about 2 MiB, held by every GPU that loads
  * the library until exit), no cudaMalloc or cudaFree.  The first call on a device looks up the
- * array's device address (cudaGetSymbolAddress); make that first call before any stream
- * capture.  All calls share the array: calls that overlap on the GPU race.  m > 1024 (or any
+ * array's device address (cudaGetSymbolAddress).  All calls share the array: calls that
+ * overlap on the GPU race.  m > 1024 (or any
  * other bad argument) returns RW_ERR_INVALID_ARG with a message in rw_last_error_message().
  * Asynchronous on `stream`.
  * ---------------------------------------------------------------------------------------- */
