@@ -48,9 +48,10 @@ def test_roofline_arithmetic():
     phases = {"seeds": 0.009, "gather": 0.027, "adapt": 0.049, "project": 0.024,
               "small": 0.019, "back": 0.016, "refine": 0.016}
     top, table = bench.rooflines(phases, N, m, lp, S, L, steps, hbm=6774.0, sm_mhz=2070.0)
-    # the dominant phase is the longest one, with the captured traffic of its kernel
+    # the dominant phase is the longest one, with the captured traffic of its kernel (null when
+    # the kernel has changed since its last capture)
     assert top["phase"] == "adapt" and top["kernel"] == "k_adapt_lu"
-    assert top["traffic"] == bench.NCU_DRAM_BYTES["k_adapt_lu"]
+    assert top["traffic"] == bench.NCU_DRAM_BYTES.get("k_adapt_lu")
     alu = 152 * 128 * 2 * 2070e6 / 1e12
     assert top["peak"] == pytest.approx(alu)
     flops = m ** 3 / 3 + 2 * L * m * m + 2 * m ** 3 / 3
