@@ -1193,7 +1193,6 @@ __device__ void adapt_body(const float* __restrict__ G, int ldg, const float* __
   if (tid == 0) mu0s = 1e-6f * red / mmax;
   __syncthreads();
   const float mu0 = mu0s;
-  int rows_done = 0;
   for (int K = 0; K * 32 < mmax; ++K) {
     const int r0 = K * 32, nr = min(32, mmax - r0);
     // tile row K of G + mu0 I (columns 0 .. r0 + nr): every element requested at once
@@ -1289,7 +1288,6 @@ __device__ void adapt_body(const float* __restrict__ G, int ldg, const float* __
       if (lane == 0) zz[k] += tot;
     }
     __syncthreads();
-    rows_done = r0 + nr;
     if (warp == 0) {  // the first candidate inside this tile that passes for every label
       for (int cb = 0; cb < ncand; cb += 32) {
         const int c = cb + lane, m = cand_m(c);
@@ -1344,13 +1342,10 @@ __device__ void adapt_body(const float* __restrict__ G, int ldg, const float* __
     const float fail_thr = 1.05f * (float)fmax;
     if (tid < RW_MAX_LABELS) s_muw[tid] = 0.f;
     __syncthreads();
-    (void)rows_done;
     for (; c < ncand; ++c) {
       m = cand_m(c);
       const int mss = m | 1;
       float* B2 = A;  // reuse the factor storage: G_m + mu I, stride mss
-      float* dk = bb;  // scratch (right-hand sides are reloaded below)
-      (void)dk;
       load_shifted_gram(B2, m, mss, G, ldg, mu0);
       __syncthreads();
       bool okc = chol_lower_smem(B2, m, mss);
