@@ -653,6 +653,71 @@ def batch_block(rw, torch, dev, repeats=3):
             **out}
 
 
+def updates_block(rw, torch, dev, hbm=HBM_FALLBACK, reps=5):
+    """The 128^3 volume's update and gradient calls (Sec. III-B; the adjoints of Eqs. rw_eq and
+    U_lin_comb): the beta update of all weights and basis values (Eq. z_ray) at m = 100, the
+    32^3 box update with beta_local = 2 beta, removal of 1% of the box's edges, and the exact
+    and eigenvector-path gradients of a squared-error loss with respect to beta and every edge
+    weight (500 seeds per label, 2 labels).  CUDA events around each call, after one untimed
+    call; the beta update's bandwidth counts the Rayleigh pass (basis row, coefficients)."""
+    J, dims, truth = synth.ellipsoid_volume(128, seed=synth.BASE_SEED + 2)
+    N = int(np.prod(dims))
+    m = 100
+    g = rw.rw_build_graph(torch.from_numpy(J.astype(np.float32)).to(dev), dims, BETA)
+    b, _ = rw.rw_precompute(g, m, tol=EIG_TOL_C3, seed=1)
+    si, sl = synth.sample_seeds(truth, dims, 500, 2, seed=synth.BASE_SEED + 2)
+    sid, sld = torch.from_numpy(si).to(dev), torch.from_numpy(sl).to(dev)
+
+    def ev_ms(fn, count):
+        fn()
+        torch.cuda.synchronize()
+        a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(count):
+            fn()
+        z.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(z) / count
+
+    out = {"workload": "rwis-128x128x128-ellipsoid-updates", "m": m, "labels": 2,
+           "seeds_per_label": 500}
+    # gradients first, on the unchanged graph
+    P = torch.empty(N, 2, device=dev)
+    rw.rw_solve_priors(g, sid, sld, 2, P)
+    U = torch.empty(N, 2, device=dev)
+    it = rw.rw_solve_pcg(g, sid, sld, 2, U, priors=P, gamma=GAMMA, prior_mode=1, iters=20000,
+                         tol=1e-6)
+    free = np.ones(N, bool)
+    free[si] = False
+    Gh = np.zeros((N, 2), np.float32)
+    Gh[free, 1] = 2 * (U.cpu().numpy()[free, 1] - truth[free])
+    G = torch.from_numpy(Gh).to(dev)
+    gw = torch.empty(3 * N, device=dev)
+    out["grad_exact"] = {"ms": ev_ms(lambda: rw.rw_grad_exact(
+        g, sid, sld, 2, P, GAMMA, U, G, gw, rel_tol=1e-6, max_iter=20000), 1),
+        "forward_pcg_iterations_to_1e-6": it, "adjoint_rel_tol": 1e-6}
+    out["grad_fast"] = {"ms": ev_ms(lambda: rw.rw_grad_fast(
+        g, b, sid, sld, 2, P, GAMMA, m, G, gw, refine_steps=3, omega=0.8), reps),
+        "refine_steps": 3}
+    # the value update with every weight recomputed (beta unchanged: the same work)
+    t = ev_ms(lambda: rw.rw_update_weights(g, b, rw.RW_UPDATE_BETA, beta=BETA), reps)
+    ld32 = (m + 3) // 4 * 4
+    rq = N * (4 * ld32 + 4 * 3 + 4)
+    out["beta_update"] = {"ms": t, "rayleigh_bytes": rq, "rayleigh_gbs": rq / (t * 1e-3) / 1e9,
+                          "frac_of_hbm": rq / (t * 1e-3) / 1e9 / hbm}
+    center = synth.boundary_voxel(truth, dims, seed=synth.BASE_SEED + 2)
+    lo, hi = synth.roi_box(center, 32, dims)
+    out["roi_update_32cubed"] = {"ms": ev_ms(lambda: rw.rw_update_weights(
+        g, b, rw.RW_UPDATE_ROI, beta=2 * BETA, roi_lo=lo, roi_hi=hi), reps)}
+    ids = synth.pick_edges(synth.roi_edge_ids(dims, lo, hi), 0.01, seed=synth.BASE_SEED + 2)
+    idd = torch.from_numpy(ids.astype(np.int64)).to(dev)
+    out["edge_removal"] = {"edges": int(ids.size), "ms": ev_ms(lambda: rw.rw_update_topology(
+        g, b, rw.RW_TOPO_REMOVE_EDGES, edge_ids=idd), reps)}
+    rw.rw_basis_free(b)
+    rw.rw_graph_free(g)
+    return out
+
+
 def registration_block(rw, torch, dev, flush, stream, n=96, m_max=150, reps=20):
     """Configuration 5, RW registration on a 96^3 fixed/moving pair (moving = fixed warped by a
     smooth random displacement field of at most 2 voxels, noise 0.03): 27 displacement labels
@@ -776,6 +841,11 @@ def gpu_arm(args):
     if args.registration_only:  # profiling runs of the registration block
         out = registration_block(rw, torch, dev, torch.empty(L2_FLUSH_BYTES // 4, device=dev),
                                  torch.cuda.current_stream())
+        if rank == 0:
+            print(json.dumps(out))
+        return 0
+    if args.updates_only:  # the 128^3 update and gradient calls
+        out = updates_block(rw, torch, dev, hbm=peaks.get("hbm_gbs") or HBM_FALLBACK)
         if rank == 0:
             print(json.dumps(out))
         return 0
@@ -1085,6 +1155,8 @@ def main():
                     help="skip the beta 90 -> 150 update-vs-recompute block")
     ap.add_argument("--c3-only", action="store_true",
                     help="only time the 128^3 workload (profiling runs)")
+    ap.add_argument("--updates-only", action="store_true",
+                    help="only time the 128^3 update and gradient calls")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
