@@ -17,9 +17,12 @@ U-hat_s = D_s^{1/2} U_s and P by P-hat = D^{1/2} P; the result is U-hat and U = 
 ``fast_rw_dense`` is a second, independent restatement for small N that forms E explicitly and
 takes its blocks literally.  Test infrastructure only.
 
-Parity note: at m < N the result is an approximation whose only pins are m = N (equality with
-the exact solve, from E F = U, Eq. pseudo_E), the agreement of the two restatements, and the
-row-sum property when D^{1/2} 1 lies in span(Q).
+Parity note: at m < N the result is an approximation.  Its pins are m = N (equality with the
+exact solve, from E F = U, Eq. pseudo_E), the agreement of the two restatements, the row-sum
+property when D^{1/2} 1 lies in span(Q), and two closed forms at m < N: exactness whenever the
+exact solution lies in span(Q) (a graph of two components with consistent seeds and priors),
+and, without seeds, the spectral filter sum_i gamma / (lambda_i + gamma) q_i q_i^T P of priors
+inside span(Q) on the unweighted grid, whose eigenvectors are DCT-II products.
 
 gamma = 0 (no priors; Sec. II-B, the paragraph after Eq. Fs).  L-hat is singular: its null vector
 is g = D^{1/2} 1 / ||D^{1/2} 1|| (g = 1 / sqrt(N) with L), E becomes the pseudo-inverse and
