@@ -22,6 +22,8 @@ definition states.  Modules:
 * ``update``    Rayleigh-quotient eigenvalue update, Eq. (z_ray) (Sec. III-B); edge edits
 * ``aggregate`` super-vertex aggregation of the basis, Eqs. (q_agg_1), (q_agg_2) (Sec. III-C)
 * ``adjoint``   gradients of a loss on U w.r.t. edge weights and beta through the exact solve
+* ``registration`` displacement labels, patch-difference priors and the unseeded solve
+                (Sec. II-A, III-A-2, IV-B)
 * ``pipeline``  the whole online solve composed from the pieces above
 
 Parity notes: the parts without a pin beyond this code itself say so in their docstrings

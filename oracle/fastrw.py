@@ -22,7 +22,9 @@ exact solve, from E F = U, Eq. pseudo_E), the agreement of the two restatements,
 property when D^{1/2} 1 lies in span(Q), and two closed forms at m < N: exactness whenever the
 exact solution lies in span(Q) (a graph of two components with consistent seeds and priors),
 and, without seeds, the spectral filter sum_i gamma / (lambda_i + gamma) q_i q_i^T P of priors
-inside span(Q) on the unweighted grid, whose eigenvectors are DCT-II products.
+inside span(Q) on the unweighted grid, whose eigenvectors are DCT-II products.  Parity
+unpinned: the value at m < N when the exact solution lies outside span(Q) (the paper judges
+that approximation only by segmentation quality).
 
 gamma = 0 (no priors; Sec. II-B, the paragraph after Eq. Fs).  L-hat is singular: its null vector
 is g = D^{1/2} 1 / ||D^{1/2} 1|| (g = 1 / sqrt(N) with L), E becomes the pseudo-inverse and
