@@ -18,7 +18,8 @@ definition states.  Modules:
 * ``fastrw``    fast RW, Eqs. (E_def)-(Fs) (Sec. II-B), factored and dense-block restatements
 * ``adaptive``  number of eigenvectors from the seeds, Eq. (alpha_1), and from priors, Eq. (g)
                 (Sec. III-A)
-* ``refine``    k steps of Jacobi-preconditioned CG on Eq. (rw_eq) from a starting guess
+* ``refine``    k damped-Jacobi (default) or Jacobi-preconditioned CG steps on Eq. (rw_eq)
+                from a starting guess (a refinement the paper does not have)
 * ``update``    Rayleigh-quotient eigenvalue update, Eq. (z_ray) (Sec. III-B); edge edits
 * ``aggregate`` super-vertex aggregation of the basis, Eqs. (q_agg_1), (q_agg_2) (Sec. III-C)
 * ``adjoint``   gradients of a loss on U w.r.t. edge weights and beta through the exact solve
